@@ -1,0 +1,166 @@
+"""Seeded synthetic Gaussian-graphical-model inputs for SPMESL.
+
+This module only draws inputs: a sparse precision matrix Theta of a given
+network type and a data matrix X with rows iid N(0, Theta^{-1}).  It contains
+none of the estimator's arithmetic (no Gram, no coordinate descent, no
+symmetrisation) and is the one module that both the FP64 oracle tests and the
+CUDA path's tests and benchmark use.
+
+Network types (Section 4.1 describes the paper's generators; the ones here are
+the workload definitions used for measurement):
+  ar1   chain graph, Theta_ii = 1, Theta_{i,i+1} = Theta_{i+1,i} = rho
+  er    Erdos-Renyi edges with probability 3/p, off-diagonal magnitudes
+        uniform in [0.1, 0.4] with a random sign
+  hub   n_hubs hub nodes, each linked to `links` distinct random non-hub
+        nodes with weight 0.25
+For er and hub the diagonal starts at 1, is shifted so that the smallest
+eigenvalue is at least 0.1, and Theta is rescaled to unit diagonal.
+
+Sampling: Theta = L L' (Cholesky), X = Z L^{-T} with Z iid N(0, 1), so that
+Cov(x) = (L L')^{-1} = Theta^{-1}.  All randomness comes from
+numpy.random.default_rng(seed) (PCG64), which is reproducible across
+platforms.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def theta_ar1(p: int, rho: float = 0.4) -> np.ndarray:
+    T = np.eye(p)
+    idx = np.arange(p - 1)
+    T[idx, idx + 1] = rho
+    T[idx + 1, idx] = rho
+    return T
+
+
+def _min_eig(T: np.ndarray) -> float:
+    p = T.shape[0]
+    if p <= 3000:
+        return float(np.linalg.eigvalsh(T)[0])
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    A = sp.csr_matrix(T)
+    # smallest algebraic eigenvalue of a sparse symmetric matrix
+    v0 = np.ones(p) / math.sqrt(p)
+    return float(spla.eigsh(A, k=1, which="SA", v0=v0, tol=1e-8,
+                            return_eigenvectors=False)[0])
+
+
+def _make_pd_unit_diag(T: np.ndarray, min_eig: float = 0.1) -> np.ndarray:
+    lam = _min_eig(T)
+    if lam < min_eig:
+        T = T + (min_eig - lam) * np.eye(T.shape[0])
+    d = 1.0 / np.sqrt(np.diag(T))
+    return T * d[:, None] * d[None, :]
+
+
+def theta_er(p: int, rng: np.random.Generator, prob: float | None = None,
+             lo: float = 0.1, hi: float = 0.4) -> np.ndarray:
+    prob = 3.0 / p if prob is None else prob
+    iu = np.triu_indices(p, k=1)
+    m = iu[0].size
+    mask = rng.random(m) < prob
+    ne = int(mask.sum())
+    vals = rng.uniform(lo, hi, ne) * rng.choice([-1.0, 1.0], ne)
+    T = np.eye(p)
+    r, c = iu[0][mask], iu[1][mask]
+    T[r, c] = vals
+    T[c, r] = vals
+    return _make_pd_unit_diag(T)
+
+
+def theta_hub(p: int, rng: np.random.Generator, n_hubs: int = 20, links: int = 50,
+              weight: float = 0.25) -> np.ndarray:
+    n_hubs = max(1, min(n_hubs, p // 2))
+    hubs = rng.choice(p, size=n_hubs, replace=False)
+    is_hub = np.zeros(p, dtype=bool)
+    is_hub[hubs] = True
+    others = np.flatnonzero(~is_hub)
+    links = min(links, others.size)
+    T = np.eye(p)
+    for h in hubs:
+        nb = rng.choice(others, size=links, replace=False)
+        T[h, nb] = weight
+        T[nb, h] = weight
+    return _make_pd_unit_diag(T)
+
+
+def sample_x(theta: np.ndarray, n: int, rng: np.random.Generator,
+             dtype=np.float32) -> np.ndarray:
+    """X (n x p, row-major) with rows iid N(0, theta^{-1})."""
+    import scipy.linalg as sla
+    L = np.linalg.cholesky(theta)
+    Z = rng.standard_normal((n, theta.shape[0]))
+    # X = Z L^{-T}  <=>  L X' = Z'
+    Xt = sla.solve_triangular(L, Z.T, lower=True)
+    return np.ascontiguousarray(Xt.T).astype(dtype)
+
+
+def make_theta(kind: str, p: int, rng: np.random.Generator) -> np.ndarray:
+    if kind == "ar1":
+        return theta_ar1(p)
+    if kind == "er":
+        return theta_er(p, rng)
+    if kind == "hub":
+        return theta_hub(p, rng)
+    if kind == "hub_scaled":
+        return theta_hub(p, rng, n_hubs=min(20, max(1, p // 10)), links=min(50, max(1, p // 4)))
+    raise ValueError(f"unknown network kind {kind!r}")
+
+
+@dataclass
+class Problem:
+    """One seeded SPMESL input."""
+    kind: str
+    p: int
+    n: int
+    seed: int
+    dtype: type
+    theta: np.ndarray
+    X: np.ndarray
+
+    @property
+    def lambda0(self) -> float:
+        # universal penalty level sqrt(2 log p / n)
+        return math.sqrt(2.0 * math.log(self.p) / self.n)
+
+
+def make_problem(kind: str, p: int, n: int, seed: int, dtype=np.float32) -> Problem:
+    rng = np.random.default_rng(seed)
+    theta = make_theta(kind, p, rng)
+    X = sample_x(theta, n, rng, dtype=dtype)
+    return Problem(kind, p, n, seed, dtype, theta, X)
+
+
+# Workloads, named by what they are.
+WORKLOADS = {
+    # AR(1) p=100 n=50, FP64 end to end, tol 1e-8, maxit 1000
+    "ar1_p100_n50_fp64": dict(kind="ar1", p=100, n=50, dtype=np.float64, tol=1e-8,
+                              maxit=1000, prec="fp64"),
+    # Erdos-Renyi p=2000 n=200, FP32 Gram and FP32 CD
+    "er_p2000_n200_fp32": dict(kind="er", p=2000, n=200, dtype=np.float32, tol=1e-6,
+                               maxit=1000, prec="fp32"),
+    # hub p=10000 n=500, split-BF16 Gram, FP32 CD, FP64 sigma / Theta
+    "hub_p10000_n500_mixed": dict(kind="hub", p=10000, n=500, dtype=np.float32, tol=1e-6,
+                                  maxit=1000, prec="mixed"),
+}
+
+
+def batch_specs(count: int = 256, seed: int = 1000, p_lo: int = 50, p_hi: int = 2000,
+                n_lo: int = 30, n_hi: int = 400):
+    """Shapes of a mixed batch: p log-uniform in [p_lo, p_hi], n uniform in
+    [n_lo, n_hi], network type uniform over ar1 / er / hub_scaled.  Fit i
+    draws its data with seed `seed + i`."""
+    rng = np.random.default_rng(seed)
+    kinds = ["ar1", "er", "hub_scaled"]
+    out = []
+    for i in range(count):
+        p = int(round(math.exp(rng.uniform(math.log(p_lo), math.log(p_hi)))))
+        n = int(rng.integers(n_lo, n_hi + 1))
+        kind = kinds[int(rng.integers(0, 3))]
+        out.append(dict(kind=kind, p=p, n=n, seed=seed + i))
+    return out
