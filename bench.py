@@ -1,0 +1,320 @@
+"""Benchmark: SPMESL solves/s on one GB300 (and N replicas under torchrun).
+
+Workload (default): Erdos-Renyi network, p = 2000, n = 200, X float32 with
+rows N(0, Theta^{-1}), lambda0 = sqrt(2 log p / n), tol 1e-6, maxit 1000,
+FP32 Gram and FP32 coordinate descent (sigma and Theta in FP64).  One step is
+one whole SPMESL solve through the C ABI: Gram S = X'X/n, standardisation,
+coordinate descent with sigma updates, Theta assembly and symmetrisation.
+Steps cycle over ten datasets (seeds 0..9), all resident in HBM.
+
+JSON line fields beyond the base contract:
+  e2e          the same metric through spmesl_solve with HOST buffers (X copied
+               in, Theta and sigma copied out, inside the timed region)
+  roofline     the coordinate-descent kernel: algorithmic bytes per launch over
+               its CUDA-event duration, against the measured HBM copy bandwidth
+  cpu_baseline the FP64 oracle on the host cores, on a bounded sample
+  latency      p50 / p99 of the per-solve device time
+  clocks       SM clocks and throttle reasons sampled during the timed region
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the same workload and prints its line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SPMESL solves/s + p99 latency, mixed-prec batched vs plain GPU @ dTheta<=1e-4"
+WORKLOAD = "er_p2000_n200_fp32"
+N_DATASETS = 10
+KERNELS_PER_SOLVE = 5        # gram, prep_diag, prep_matrix, cd_column, theta
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(count: int):
+    import numpy as np
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    probs = [synth.make_problem(w["kind"], w["p"], w["n"], s, dtype=np.float32)
+             for s in range(count)]
+    return w, probs
+
+
+def cpu_baseline(w, prob, budget_s: float = 20.0):
+    """FP64 oracle (as it stands) on the host cores: one whole solve (Gram +
+    Algorithm 2) of dataset seed 0, repeated while it stays inside the budget."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    X64 = prob.X.astype(np.float64)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        S = oracle.gram(X64)
+        oracle.spmesl(S, prob.lambda0, tol=w["tol"], maxit=w["maxit"], nthreads=cores)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 5:
+            break
+    t = statistics.median(times)
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} whole solves (FP64 Gram + Algorithm 2, OpenMP over columns) "
+                      f"of the ER p={prob.p} n={prob.n} dataset seed 0, median {t:.3f} s"}
+
+
+def run_reference(args):
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return
+    w, probs = make_inputs(1)
+    cb = cpu_baseline(w, probs[0], budget_s=max(5.0, 3.0 * args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "p": probs[0].p, "n": probs[0].n,
+                       "network": "erdos_renyi", "lambda0": "sqrt(2 log p / n)",
+                       "tol": w["tol"], "maxit": w["maxit"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2203_15031_gb300 as sp
+
+    rank, local_rank, world = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sp.lib()
+
+    w, probs = make_inputs(N_DATASETS)
+    p, n = w["p"], w["n"]
+    lam = probs[0].lambda0
+    Xd = [torch.from_numpy(pr.X).to(dev) for pr in probs]
+    S = torch.empty((p, p), dtype=torch.float32, device=dev)
+    Theta = torch.empty((p, p), dtype=torch.float64, device=dev)
+    sigma = torch.empty(p, dtype=torch.float64, device=dev)
+    gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
+    fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
+    gkeep, gws = sp._workspace(gnb, dev)
+    fkeep, fws = sp._workspace(fnb, dev)
+    opts = sp.spmesl_default_opts()
+    opts.precision = sp.FP32
+    opts.record_phase_times = 1
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        X = Xd[i % N_DATASETS]
+        rc = sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S, p, gws, gnb, stream)
+        if rc != 0:
+            raise sp.SpmeslError(rc, "spmesl_gram")
+        rc = sp.spmesl_fit(S, n, p, lam, w["tol"], w["maxit"], opts, Theta, sigma, None, fws,
+                           fnb, stream)
+        if rc != 0:
+            raise sp.SpmeslError(rc, "spmesl_fit")
+
+    st = sp.Stats()
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sp._check(sp.spmesl_fit_result(fws, p, sp.FP32, st, stream), "warmup", ok=(0,))
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cd_ms, moves, sweeps = [], [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()                     # evict X / S from L2 between solves
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+            # phase times and counters of this solve (read after the event pair)
+            stream.synchronize()
+            sp.spmesl_fit_result(fws, p, sp.FP32, st, stream)
+            cd_ms.append(st.ms_cd)
+            moves.append(st.moves)
+            sweeps.append(st.inner_sweeps)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(per)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned)
+    Xh = [torch.from_numpy(pr.X).pin_memory() for pr in probs]
+    Th = torch.empty((p, p), dtype=torch.float64).pin_memory()
+    sh = torch.empty(p, dtype=torch.float64).pin_memory()
+    snb = sp.spmesl_solve_workspace_bytes(n, p, sp.FP32)
+    skeep, sws = sp._workspace(snb, dev)
+    sopts = sp.spmesl_default_opts()
+    sopts.precision = sp.FP32
+    for i in range(args.warmup):
+        sp._check(sp.spmesl_solve(Xh[i % N_DATASETS], n, p, lam, w["tol"], w["maxit"], sopts, Th,
+                                  sh, None, sws, snb, stream), "spmesl_solve")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        sp._check(sp.spmesl_solve(Xh[i % N_DATASETS], n, p, lam, w["tol"], w["maxit"], sopts, Th,
+                                  sh, None, sws, snb, stream), "spmesl_solve")
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        dist.barrier()
+    e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": n * p * 4, "d2h_bytes_per_step": p * p * 8 + p * 8}
+
+    if rank == 0:
+        hbm, which = _peaks()
+        # algorithmic bytes of one CD launch: every column loads S_.j once into
+        # shared memory and writes b_j once; every coordinate move reads one
+        # S row (the column slice of the rank-1 update).
+        ldp = (p + 31) // 32 * 32
+        mv = statistics.mean(moves)
+        bytes_cd = 4.0 * ldp * (2 * p + mv)
+        cd_mean_ms = statistics.mean(cd_ms)
+        achieved = bytes_cd / (cd_mean_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": "cd_column_kernel<float>",
+                "peak_kind": which, "algorithmic_bytes_per_launch": bytes_cd,
+                "mean_launch_ms": cd_mean_ms, "moves_per_launch": mv,
+                "sweeps_per_launch": statistics.mean(sweeps)}
+        per_sorted = sorted(per)
+        lat = {"p50_ms": statistics.median(per),
+               "p99_ms": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
+               "unit": "ms per solve (device)"}
+        cb = cpu_baseline(w, probs[0]) if world == 1 and not args.no_cpu_baseline else None
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "p": p, "n": n, "network": "erdos_renyi",
+                           "datasets": N_DATASETS, "lambda0": "sqrt(2 log p / n)",
+                           "tol": w["tol"], "maxit": w["maxit"], "gram": "fp32",
+                           "inner_rule": "column", "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"replicas x{world}"},
+                "latency": lat, "e2e": e2e, "roofline": roof, "cpu_baseline": cb,
+                "gpu_launches": KERNELS_PER_SOLVE * args.steps,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    del gkeep, fkeep, skeep
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

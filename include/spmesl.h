@@ -1,0 +1,212 @@
+/*
+ * spmesl.h - C ABI of libspmesl: sparse precision matrix estimation via the
+ * scaled lasso (SPMESL), solved by GPU-parallel coordinate descent on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are dense and row-major.  "p x p" buffers are p*p elements with
+ *    leading dimension p unless a leading-dimension argument says otherwise.
+ *  - Pointers are DEVICE pointers unless the argument name ends in `_host`.
+ *    The caller allocates and owns every buffer it passes; the library never
+ *    frees or keeps a caller pointer after the call's stream work completes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued on it; calls return without synchronising unless
+ *    the description says otherwise.
+ *  - Errors come back as spmesl_status codes; nothing throws across the ABI.
+ *    Invalid arguments are rejected on the host before any work is enqueued.
+ *    Conditions found on the device (non-finite input, sigma floor, iteration
+ *    caps, a bounded wait that ran out) are written to a status word in the
+ *    workspace and reported by spmesl_fit_result (or by spmesl_fit itself
+ *    when `stats` is non-NULL).
+ *  - Precision: SPMESL_FP64 takes FP64 data and works in FP64 throughout.
+ *    SPMESL_FP32 and SPMESL_MIXED take FP32 data, run the coordinate-descent
+ *    sweeps in FP32, and keep sigma, the convergence decisions on sigma and
+ *    the final Theta in FP64.  SPMESL_MIXED builds the Gram matrix with
+ *    split-BF16 tensor-core products and FP32 accumulation.
+ *
+ * Index convention for the result: Theta[j*p + k] = omega_jk.  Before
+ * symmetrisation column k of Omega comes from regression k (Eq. (4)):
+ * omega_kk = 1/sigma_k^2, omega_jk = -b_jk / sigma_k^2, where b_jk is the
+ * coefficient of x_j in the regression of x_k on the other columns.
+ */
+#ifndef SPMESL_H
+#define SPMESL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPMESL_OK = 0,
+    SPMESL_NOT_CONVERGED = 1,   /* an iteration cap was hit; outputs hold the last iterate */
+    SPMESL_EINVAL = -1,         /* bad argument (sizes, pointers, tolerances, workspace) */
+    SPMESL_ENOMEM = -2,         /* workspace too small / allocation or budget refused */
+    SPMESL_ENONFINITE = -3,     /* NaN/Inf in the input, or S_jj <= 0 */
+    SPMESL_EDEGENERATE = -4,    /* some sigma_j^2 reached the floor 1e-12 * S_jj (perfect fit) */
+    SPMESL_ETIMEOUT = -5,       /* a bounded device-side wait ran out */
+    SPMESL_ECUDA = -6,          /* a CUDA runtime call failed */
+    SPMESL_EBUSY = -7,          /* request still running / no free slot */
+    SPMESL_ENOTFOUND = -8       /* unknown ticket */
+} spmesl_status;
+
+typedef enum {
+    SPMESL_FP64 = 0,
+    SPMESL_FP32 = 1,
+    SPMESL_MIXED = 2
+} spmesl_precision;
+
+/* Penalty level lambda0 (Section 2.1 and Section 2.3, Eqs. (10)-(11)). */
+typedef enum {
+    SPMESL_LAMBDA_GIVEN = 0,    /* use the lambda0 argument as is */
+    SPMESL_LAMBDA_UNIV = 1,     /* sqrt(2 log(p) / n)                         (Section 2.1) */
+    SPMESL_LAMBDA_UNIV_PM1 = 2, /* sqrt(2 log(p-1) / n)                       (Section 4.1) */
+    SPMESL_LAMBDA_UB = 3,       /* sqrt(4 log(p) / n)                         (Eq. (10), A = 1) */
+    SPMESL_LAMBDA_PB = 4        /* sqrt(2) L_n(k/p), k = L_1^4(k/p)+2L_1^2(k/p) (Eq. (11)) */
+} spmesl_lambda_rule;
+
+/* Inner stopping rule of the lasso subproblems. */
+typedef enum {
+    SPMESL_INNER_JOINT = 0,     /* ||B_next - B_cur||_inf over all active columns (Algorithm 3) */
+    SPMESL_INNER_COLUMN = 1     /* per column ||b_next - b_cur||_inf (Algorithms 1-2) */
+} spmesl_inner_rule;
+
+typedef struct {
+    int32_t precision;          /* spmesl_precision */
+    int32_t standardize;        /* 1 (default): fit on S^C = C S C, C = diag(S_jj^-1/2), and
+                                   return C Omega^C C (Proposition 1); 0: fit on S itself with
+                                   update b_kj = Soft(c, lambda0 sigma_j) / S_kk */
+    int32_t center;             /* spmesl_gram / spmesl_solve: subtract column means (Section 2.2) */
+    int32_t lambda_rule;        /* spmesl_lambda_rule */
+    int32_t inner_rule;         /* spmesl_inner_rule (default SPMESL_INNER_COLUMN) */
+    int32_t warps_per_block;    /* 0 = chosen from p and shared-memory capacity */
+    int32_t record_phase_times; /* 1: record CUDA events around the fit's phases on `stream`;
+                                   spmesl_fit_result then fills ms_cd and ms_theta */
+    int32_t reserved[9];
+} spmesl_opts;
+
+typedef struct {
+    int32_t status;             /* spmesl_status of the fit */
+    int32_t outer_iters;        /* max over columns of sigma iterations (joint rule: global count) */
+    int64_t inner_sweeps;       /* sum over columns of full sweeps (joint rule: global count) */
+    int64_t moves;              /* coordinate updates that changed some b_kj (one S-row axpy each) */
+    int64_t nnz_B;              /* nonzero off-diagonal b_jk at exit */
+    int32_t n_not_converged;    /* columns that hit an iteration cap */
+    int32_t n_degenerate;       /* columns whose sigma^2 hit the floor */
+    double max_db;              /* largest |delta b| of the last sweep (joint rule) */
+    double lambda0;             /* penalty level actually used */
+    float ms_gram;              /* device time of the Gram step (spmesl_solve only), ms */
+    float ms_fit;               /* device time of the whole fit, ms */
+    float ms_cd;                /* coordinate-descent kernel alone (record_phase_times), ms */
+    float ms_theta;             /* Theta assembly kernel alone (record_phase_times), ms */
+    int64_t reserved[3];
+} spmesl_stats;
+
+/* Fill `opts` with the defaults: FP32, standardize = 1, center = 0,
+ * lambda_rule = GIVEN, inner_rule = COLUMN, warps_per_block = 0. */
+void spmesl_default_opts(spmesl_opts* opts);
+
+/* Static text for a status code. */
+const char* spmesl_status_string(int status);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int spmesl_version(void);
+
+/* Penalty level for a rule (host computation; Section 2.1, Eqs. (10)-(11),
+ * Section 4.1).  Returns NaN for SPMESL_LAMBDA_GIVEN or invalid n, p. */
+double spmesl_lambda(int rule, int n, int p);
+
+/*
+ * Gram matrix S = X'X / n (Section 2.2), optionally of the column-centred X.
+ *   X          n x p, leading dimension ldx >= p; FP64 for SPMESL_FP64,
+ *              FP32 otherwise.  Read only.
+ *   S          p x p output, leading dimension lds >= p, same element type as
+ *              X.  Both triangles are written.
+ *   workspace  device scratch of at least spmesl_gram_workspace_bytes(n, p,
+ *              precision) bytes (may be NULL when that is 0).
+ * SPMESL_FP64 and SPMESL_FP32 accumulate in the input precision on the CUDA
+ * cores; SPMESL_MIXED splits X = hi + lo into two BF16 parts and forms
+ * hi'hi + hi'lo + lo'hi on the tensor cores (tcgen05, TMEM accumulators)
+ * with FP32 accumulation.
+ * Errors: EINVAL for n < 1, p < 1, ldx < p, lds < p, NULL pointers, a short
+ * workspace; ECUDA if a launch fails.
+ */
+size_t spmesl_gram_workspace_bytes(int n, int p, int precision);
+spmesl_status spmesl_gram(const void* X, int n, int p, int ldx, int precision, int center,
+                          void* S, int lds, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * One SPMESL fit on a covariance matrix (Algorithm 2 / Algorithm 3):
+ *   1. S^C = C S C (standardize = 1, Section 2.2 and Proposition 1);
+ *   2. for every column j, the scaled lasso of Eq. (5) by cyclic ascending
+ *      coordinate descent with warm start (Algorithm 1): all columns run in
+ *      parallel, each keeping its gradient g_j = S_.j - S b_j on chip and
+ *      applying the rank-1 update g_j -= S_.k delta_kj after every coordinate
+ *      that moves (Proposition 2 written on S); sigma_j^2 =
+ *      S_jj - 2 b_j'S_.j + b_j'S b_j in FP64 (Eq. (14)); columns whose sigma
+ *      changed by less than tol are retired (Section 3.3);
+ *   3. Omega_1 = -B D (Eq. (4)), min-magnitude symmetrisation (Eq. (9)), and
+ *      Omega^o = C Omega^C C.
+ *   S          p x p covariance (FP64 for SPMESL_FP64, FP32 otherwise), read only.
+ *   n          sample size; used only by lambda rules other than GIVEN (may be 0
+ *              with SPMESL_LAMBDA_GIVEN).
+ *   lambda0    penalty level (> 0) when opts->lambda_rule is GIVEN.
+ *   tol        the tolerance delta of both stopping tests (> 0).
+ *   maxit      cap on inner sweeps per lasso subproblem and, separately, on
+ *              sigma iterations (>= 1).
+ *   opts       may be NULL for the defaults; opts->precision selects the path.
+ *   Theta      p x p FP64 output (row-major, symmetric).
+ *   sigma      p FP64 output, sigma_j in the original scale.
+ *   stats      host pointer or NULL.  Non-NULL makes the call synchronise on
+ *              `stream` and fill it; the return value is then the fit's status.
+ *   workspace  device scratch of at least spmesl_fit_workspace_bytes(p,
+ *              precision) bytes, 256-byte aligned.  It holds the standardised
+ *              S, the coefficients B and the fit's control block, and must not
+ *              be reused until the fit has completed on `stream`.
+ * Returns OK once the work is enqueued (stats == NULL) or the fit's status.
+ * Errors: EINVAL (p < 2, lambda0 <= 0, tol <= 0, maxit < 1, NULL pointers,
+ * misaligned or short workspace, p above spmesl_max_p(precision)); ECUDA.
+ * Device-detected: ENONFINITE (non-finite S or S_jj <= 0; Theta untouched),
+ * EDEGENERATE, NOT_CONVERGED, ETIMEOUT.
+ */
+size_t spmesl_fit_workspace_bytes(int p, int precision);
+int spmesl_max_p(int precision);
+spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol, int maxit,
+                         const spmesl_opts* opts, double* Theta, double* sigma,
+                         spmesl_stats* stats, void* workspace, size_t ws_bytes, void* stream);
+
+/* Synchronise `stream` and read the status and counters of the last fit that
+ * ran in `workspace` (p and precision as given to spmesl_fit).  Returns the
+ * fit's status. */
+spmesl_status spmesl_fit_result(const void* workspace, int p, int precision,
+                                spmesl_stats* stats, void* stream);
+
+/* Copy the coefficients of the last fit in `workspace` to B (p x p FP64
+ * device buffer, original scale, B[j*p + k] = b_jk, zero diagonal). */
+spmesl_status spmesl_fit_coefficients(const void* workspace, int p, int precision, double* B,
+                                      void* stream);
+
+/*
+ * End-to-end solve from HOST data: copies X_host to the device, builds S
+ * (spmesl_gram), fits (spmesl_fit), copies Theta and sigma back to the host
+ * buffers and synchronises `stream`.
+ *   X_host      n x p row-major host buffer (FP64 for SPMESL_FP64, else FP32);
+ *               pinned memory gives the fastest copies.
+ *   Theta_host  p x p FP64 host output; sigma_host p FP64 host output.
+ *   workspace   device scratch of spmesl_solve_workspace_bytes(n, p, precision).
+ * Returns the fit's status (errors as spmesl_gram and spmesl_fit).
+ */
+size_t spmesl_solve_workspace_bytes(int n, int p, int precision);
+spmesl_status spmesl_solve(const void* X_host, int n, int p, double lambda0, double tol,
+                           int maxit, const spmesl_opts* opts, double* Theta_host,
+                           double* sigma_host, spmesl_stats* stats, void* workspace,
+                           size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMESL_H */

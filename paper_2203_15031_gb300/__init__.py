@@ -1,0 +1,289 @@
+"""Python binding of libspmesl (SPMESL by GPU-parallel coordinate descent on GB300).
+
+Argument marshalling only: every step of the estimator runs in the CUDA
+library declared in ``include/spmesl.h``.  PyTorch supplies device memory and
+the current CUDA stream.  There is no CPU fallback: if the library cannot be
+built or loaded, or no CUDA device is present, the calls raise.
+
+Low-level: ``lib()`` returns the ctypes handle; every C entry point is also
+exposed here under its C name (``spmesl_gram``, ``spmesl_fit``, ...), taking
+torch tensors or raw integers for pointers.
+
+Convenience wrappers: ``gram``, ``fit``, ``solve``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import _build
+
+__all__ = [
+    "SPMESL_OK", "SPMESL_NOT_CONVERGED", "SPMESL_EINVAL", "SPMESL_ENOMEM", "SPMESL_ENONFINITE",
+    "SPMESL_EDEGENERATE", "SPMESL_ETIMEOUT", "SPMESL_ECUDA", "SPMESL_EBUSY", "SPMESL_ENOTFOUND",
+    "FP64", "FP32", "MIXED", "Opts", "Stats", "SpmeslError", "lib", "build",
+    "spmesl_default_opts", "spmesl_status_string", "spmesl_version", "spmesl_lambda",
+    "spmesl_max_p", "spmesl_gram_workspace_bytes", "spmesl_gram", "spmesl_fit_workspace_bytes",
+    "spmesl_fit", "spmesl_fit_result", "spmesl_fit_coefficients", "spmesl_solve_workspace_bytes",
+    "spmesl_solve", "gram", "fit", "solve",
+]
+
+SPMESL_OK, SPMESL_NOT_CONVERGED = 0, 1
+SPMESL_EINVAL, SPMESL_ENOMEM, SPMESL_ENONFINITE, SPMESL_EDEGENERATE = -1, -2, -3, -4
+SPMESL_ETIMEOUT, SPMESL_ECUDA, SPMESL_EBUSY, SPMESL_ENOTFOUND = -5, -6, -7, -8
+FP64, FP32, MIXED = 0, 1, 2
+LAMBDA_GIVEN, LAMBDA_UNIV, LAMBDA_UNIV_PM1, LAMBDA_UB, LAMBDA_PB = 0, 1, 2, 3, 4
+INNER_JOINT, INNER_COLUMN = 0, 1
+_PREC = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("standardize", ctypes.c_int32),
+                ("center", ctypes.c_int32), ("lambda_rule", ctypes.c_int32),
+                ("inner_rule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("record_phase_times", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
+                ("inner_sweeps", ctypes.c_int64), ("moves", ctypes.c_int64),
+                ("nnz_B", ctypes.c_int64), ("n_not_converged", ctypes.c_int32),
+                ("n_degenerate", ctypes.c_int32), ("max_db", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("ms_gram", ctypes.c_float),
+                ("ms_fit", ctypes.c_float), ("ms_cd", ctypes.c_float),
+                ("ms_theta", ctypes.c_float), ("reserved", ctypes.c_int64 * 3)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class SpmeslError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {spmesl_status_string(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+_vp, _sz, _i32, _dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "spmesl_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "spmesl_status_string": (ctypes.c_char_p, [_i32]),
+    "spmesl_version": (_i32, []),
+    "spmesl_lambda": (_dbl, [_i32, _i32, _i32]),
+    "spmesl_max_p": (_i32, [_i32]),
+    "spmesl_gram_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "spmesl_gram": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "spmesl_fit_workspace_bytes": (_sz, [_i32, _i32]),
+    "spmesl_fit": (_i32, [_vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts), _vp, _vp,
+                          ctypes.POINTER(Stats), _vp, _sz, _vp]),
+    "spmesl_fit_result": (_i32, [_vp, _i32, _i32, ctypes.POINTER(Stats), _vp]),
+    "spmesl_fit_coefficients": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "spmesl_solve_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "spmesl_solve": (_i32, [_vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts), _vp, _vp,
+                            ctypes.POINTER(Stats), _vp, _sz, _vp]),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile libspmesl.so for sm_103a (see _build.py)."""
+    return _build.build(force=force)
+
+
+def lib():
+    """Load (building first if needed) and return the ctypes handle."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            h = ctypes.CDLL(_build.build())
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(h, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = h
+    return _lib
+
+
+# ----------------------------------------------------------------------------- helpers
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):          # numpy host buffer
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)!r}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, where: str, ok=(SPMESL_OK,)):
+    if status not in ok:
+        raise SpmeslError(status, where)
+    return status
+
+
+def _require_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libspmesl needs a CUDA device; there is no CPU fallback")
+
+
+def _workspace(nbytes: int, device):
+    import torch
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf, buf.data_ptr() + off
+
+
+# ----------------------------------------------------------------------------- C names
+def spmesl_default_opts() -> Opts:
+    o = Opts()
+    lib().spmesl_default_opts(ctypes.byref(o))
+    return o
+
+
+def spmesl_status_string(status: int) -> str:
+    return lib().spmesl_status_string(int(status)).decode()
+
+
+def spmesl_version() -> int:
+    return lib().spmesl_version()
+
+
+def spmesl_lambda(rule: int, n: int, p: int) -> float:
+    return lib().spmesl_lambda(int(rule), int(n), int(p))
+
+
+def spmesl_max_p(precision: int) -> int:
+    return lib().spmesl_max_p(int(precision))
+
+
+def spmesl_gram_workspace_bytes(n: int, p: int, precision: int) -> int:
+    return lib().spmesl_gram_workspace_bytes(n, p, precision)
+
+
+def spmesl_gram(X, n, p, ldx, precision, center, S, lds, workspace, ws_bytes, stream=None) -> int:
+    return lib().spmesl_gram(_ptr(X), n, p, ldx, precision, int(center), _ptr(S), lds,
+                             _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def spmesl_fit_workspace_bytes(p: int, precision: int) -> int:
+    return lib().spmesl_fit_workspace_bytes(p, precision)
+
+
+def spmesl_fit(S, n, p, lambda0, tol, maxit, opts, Theta, sigma, stats, workspace, ws_bytes,
+               stream=None) -> int:
+    return lib().spmesl_fit(_ptr(S), n, p, lambda0, tol, maxit,
+                            ctypes.byref(opts) if opts is not None else None, _ptr(Theta),
+                            _ptr(sigma), ctypes.byref(stats) if stats is not None else None,
+                            _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def spmesl_fit_result(workspace, p, precision, stats, stream=None) -> int:
+    return lib().spmesl_fit_result(_ptr(workspace), p, precision,
+                                   ctypes.byref(stats) if stats is not None else None,
+                                   _stream(stream))
+
+
+def spmesl_fit_coefficients(workspace, p, precision, B, stream=None) -> int:
+    return lib().spmesl_fit_coefficients(_ptr(workspace), p, precision, _ptr(B), _stream(stream))
+
+
+def spmesl_solve_workspace_bytes(n: int, p: int, precision: int) -> int:
+    return lib().spmesl_solve_workspace_bytes(n, p, precision)
+
+
+def spmesl_solve(X_host, n, p, lambda0, tol, maxit, opts, Theta_host, sigma_host, stats,
+                 workspace, ws_bytes, stream=None) -> int:
+    return lib().spmesl_solve(_ptr(X_host), n, p, lambda0, tol, maxit,
+                              ctypes.byref(opts) if opts is not None else None, _ptr(Theta_host),
+                              _ptr(sigma_host), ctypes.byref(stats) if stats is not None else None,
+                              _ptr(workspace), ws_bytes, _stream(stream))
+
+
+# ----------------------------------------------------------------------------- wrappers
+def _prec(precision) -> int:
+    return _PREC[precision] if isinstance(precision, str) else int(precision)
+
+
+def gram(X, precision="fp32", center=False, stream=None):
+    """S = X'X/n for a CUDA tensor X (n x p); returns a new p x p tensor."""
+    import torch
+    _require_cuda()
+    prec = _prec(precision)
+    n, p = X.shape
+    X = X.contiguous()
+    S = torch.empty((p, p), dtype=X.dtype, device=X.device)
+    nb = spmesl_gram_workspace_bytes(n, p, prec)
+    keep, ws = _workspace(max(nb, 1), X.device)
+    _check(spmesl_gram(X, n, p, p, prec, center, S, p, ws, nb, stream), "spmesl_gram")
+    del keep
+    return S
+
+
+def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=True,
+        inner_rule=INNER_COLUMN, lambda_rule=LAMBDA_GIVEN, warps_per_block=0,
+        return_B=False, stream=None):
+    """One fit on a CUDA covariance tensor.  Synchronises and returns
+    (Theta, sigma, stats_dict[, B])."""
+    import torch
+    _require_cuda()
+    prec = _prec(precision)
+    p = S.shape[0]
+    opts = spmesl_default_opts()
+    opts.precision = prec
+    opts.standardize = int(bool(standardize))
+    opts.inner_rule = int(inner_rule)
+    opts.lambda_rule = int(lambda_rule)
+    opts.warps_per_block = int(warps_per_block)
+    Theta = torch.empty((p, p), dtype=torch.float64, device=S.device)
+    sigma = torch.empty(p, dtype=torch.float64, device=S.device)
+    nb = spmesl_fit_workspace_bytes(p, prec)
+    keep, ws = _workspace(nb, S.device)
+    st = Stats()
+    rc = spmesl_fit(S.contiguous(), n, p, lambda0, tol, maxit, opts, Theta, sigma, st, ws, nb,
+                    stream)
+    _check(rc, "spmesl_fit", ok=(SPMESL_OK, SPMESL_NOT_CONVERGED))
+    out = [Theta, sigma, st.as_dict()]
+    if return_B:
+        B = torch.empty((p, p), dtype=torch.float64, device=S.device)
+        _check(spmesl_fit_coefficients(ws, p, prec, B, stream), "spmesl_fit_coefficients")
+        torch.cuda.current_stream().synchronize()
+        out.append(B)
+    del keep
+    return tuple(out)
+
+
+def solve(X_host, lambda0, tol=1e-6, maxit=1000, precision="fp32", center=False,
+          inner_rule=INNER_COLUMN, stream=None):
+    """End-to-end solve from a host (numpy) X; returns (Theta, sigma, stats)."""
+    import numpy as np
+    import torch
+    _require_cuda()
+    prec = _prec(precision)
+    n, p = X_host.shape
+    dt = np.float64 if prec == FP64 else np.float32
+    X_host = np.ascontiguousarray(X_host, dtype=dt)
+    Theta = np.empty((p, p), dtype=np.float64)
+    sigma = np.empty(p, dtype=np.float64)
+    opts = spmesl_default_opts()
+    opts.precision = prec
+    opts.center = int(bool(center))
+    opts.inner_rule = int(inner_rule)
+    nb = spmesl_solve_workspace_bytes(n, p, prec)
+    keep, ws = _workspace(nb, torch.device("cuda", torch.cuda.current_device()))
+    st = Stats()
+    rc = spmesl_solve(X_host, n, p, lambda0, tol, maxit, opts, Theta, sigma, st, ws, nb, stream)
+    _check(rc, "spmesl_solve", ok=(SPMESL_OK, SPMESL_NOT_CONVERGED))
+    del keep
+    return Theta, sigma, st.as_dict()

@@ -1,0 +1,118 @@
+// Internal definitions shared by the libspmesl translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spmesl.h"
+
+namespace spmesl {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Column status bits written by the fit kernels (a column may carry both).
+constexpr int COL_OK = 0;
+constexpr int COL_NOT_CONVERGED = 1;
+constexpr int COL_DEGENERATE = 2;
+
+// Device-side error codes stored in FitCtrl::err (0 = none).
+constexpr int DEV_ERR_NONFINITE = 1;
+constexpr int DEV_ERR_TIMEOUT = 2;
+
+// Upper bound of any bounded spin wait (ns of %globaltimer).
+constexpr unsigned long long SPIN_LIMIT_NS = 4000000000ull;
+
+// Control block at the start of a fit workspace.  Zeroed before every fit.
+struct FitCtrl {
+    unsigned int bar_count;       // grid barrier arrivals
+    unsigned int bar_gen;         // grid barrier generation
+    int err;                      // DEV_ERR_* (first error wins)
+    int n_active;                 // joint rule: active columns of the current outer iteration
+    int next_col;                 // column rule: dynamic work counter
+    int outer_max;                // max sigma iterations over columns (joint: global)
+    int n_not_converged;
+    int n_degenerate;
+    unsigned long long sweep_max[3];   // joint rule: max|delta| per sweep, as ordered bits
+    unsigned long long total_sweeps;   // sum over columns (joint: global sweep count)
+    unsigned long long moves;          // coordinate updates that changed b
+    unsigned long long max_db_bits;    // joint rule: max|delta| of the last sweep (double bits)
+    unsigned long long nnz;            // nonzero b at exit
+    int inner_cap_hit;                 // joint rule: inner cap reached in some outer iteration
+    int pad[7];
+};
+static_assert(sizeof(FitCtrl) <= 256, "FitCtrl must fit its 256-byte slot");
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline int elem_size(int precision) { return precision == SPMESL_FP64 ? 8 : 4; }
+
+// Leading dimension of the per-column p-vectors in the workspace: a multiple
+// of 32 elements, so every row starts on a 128-byte (FP32) or 256-byte (FP64)
+// boundary and 16-byte vector loads never straddle a row.
+inline int padded_ld(int p) { return (p + 31) / 32 * 32; }
+
+// Byte offsets of the fit workspace (see spmesl_fit_workspace_bytes).
+struct FitLayout {
+    int ldp;
+    size_t ctrl, cs, sigma, col_status, active, active_next, flag, diag, SC, BT, GT, total;
+};
+
+inline FitLayout fit_layout(int p, int precision) {
+    FitLayout L{};
+    const size_t s = (size_t)elem_size(precision);
+    L.ldp = padded_ld(p);
+    const size_t mat = align_up((size_t)p * (size_t)L.ldp * s, 256);
+    size_t off = 0;
+    L.ctrl = off;        off += 256;
+    L.cs = off;          off += align_up((size_t)p * 8, 256);
+    L.sigma = off;       off += align_up((size_t)p * 8, 256);
+    L.col_status = off;  off += align_up((size_t)p * 4, 256);
+    L.active = off;      off += align_up((size_t)p * 4, 256);
+    L.active_next = off; off += align_up((size_t)p * 4, 256);
+    L.flag = off;        off += align_up((size_t)p * 4, 256);
+    L.diag = off;        off += align_up((size_t)p * s, 256);
+    L.SC = off;          off += mat;
+    L.BT = off;          off += mat;
+    L.GT = off;          off += mat;
+    L.total = off;
+    return L;
+}
+
+// 16-byte vector of T.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Record the first device-side error.
+__device__ __forceinline__ void set_error(FitCtrl* c, int code) { atomicCAS(&c->err, 0, code); }
+
+}  // namespace spmesl
+
+// Launchers implemented in the .cu files (host side, stream-ordered).
+namespace spmesl {
+cudaError_t launch_gram(const void* X, int n, int p, int ldx, int precision, int center, void* S,
+                        int lds, void* ws, cudaStream_t st);
+size_t gram_ws_bytes(int n, int p, int precision);
+
+struct FitLaunch {
+    const void* S;       // input covariance (p x p, ld p)
+    int p;
+    double lambda0, tol;
+    int maxit;
+    int precision, standardize, inner_rule, warps_per_block;
+    double* Theta;
+    double* sigma_out;
+    unsigned char* ws;   // workspace base
+    cudaEvent_t* phase_events;   // nullptr, or 3 events: before CD, after CD, after Theta
+};
+cudaError_t launch_fit(const FitLaunch& f, cudaStream_t st);
+cudaError_t launch_export_B(const unsigned char* ws, int p, int precision, double* B,
+                            cudaStream_t st);
+int max_p_for(int precision);
+}  // namespace spmesl

@@ -148,3 +148,36 @@ def kkt_residual(S: np.ndarray, B: np.ndarray, sigma: np.ndarray, lambda0: float
     q = np.array([W[k, k] - 2 * Bc[:, k] @ W[:, k] + Bc[:, k] @ W @ Bc[:, k] for k in range(p)])
     sig_err = float(np.max(np.abs(np.sqrt(np.maximum(q, 0)) - sc) / sc))
     return viol, sig_err
+
+
+def compare_theta(T_gpu: np.ndarray, T_ref: np.ndarray, B_ref: np.ndarray, sigma_ref: np.ndarray,
+                  rel: float = 1e-4, supp_rel: float = 1e-6):
+    """Parity of a symmetrised Theta against the oracle's, element by element.
+
+    Eq. (9) keeps the smaller-magnitude of two candidates; when the oracle's
+    two candidates are within the tolerance of each other in magnitude the
+    choice is not determined at that precision, so either candidate is
+    accepted there.  Supports must agree except where the nonzero side is
+    below supp_rel * max|Theta|.  Returns a dict of diagnostics; 'ok' is the
+    verdict."""
+    p = T_ref.shape[0]
+    scale = float(np.max(np.abs(T_ref)))
+    tol = rel * scale
+    T1 = -B_ref / sigma_ref[None, :] ** 2               # unsymmetrised, column k = regression k
+    err = np.abs(T_gpu - T_ref)
+    bad = err > tol
+    if bad.any():
+        j, k = np.nonzero(bad)
+        a, b = T1[j, k], T1[k, j]
+        ambiguous = np.abs(np.abs(a) - np.abs(b)) <= tol
+        near_other = np.minimum(np.abs(T_gpu[j, k] - a), np.abs(T_gpu[j, k] - b)) <= tol
+        still = ~(ambiguous & near_other)
+        nbad = int(still.sum())
+    else:
+        nbad = 0
+    small = supp_rel * scale
+    supp_mismatch = (T_gpu != 0) != (T_ref != 0)
+    supp_mismatch &= np.maximum(np.abs(T_gpu), np.abs(T_ref)) >= small
+    return dict(ok=(nbad == 0 and not supp_mismatch.any()), max_abs_err=float(err.max()),
+                max_rel_err=float(err.max() / scale), n_bad=nbad,
+                n_support_mismatch=int(supp_mismatch.sum()), scale=scale)

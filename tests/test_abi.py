@@ -1,0 +1,93 @@
+"""The C-ABI library builds for sm_103a, loads and exports every symbol that
+include/*.h declares; host-only entry points behave (no GPU needed)."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import json
+import math
+import os
+import re
+
+import pytest
+
+import paper_2203_15031_gb300 as sp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(spmesl_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = sp.build()
+    h = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(h, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    for n in declared_functions():
+        assert hasattr(sp, n), n
+
+
+def test_defaults_version_status_strings():
+    o = sp.spmesl_default_opts()
+    assert o.precision == sp.FP32 and o.standardize == 1 and o.center == 0
+    assert o.inner_rule == sp.INNER_COLUMN
+    assert sp.spmesl_version() >= 10000
+    assert "invalid" in sp.spmesl_status_string(sp.SPMESL_EINVAL)
+    assert sp.spmesl_status_string(0) == "ok"
+
+
+def test_host_penalty_levels_match_paper_example():
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "lambda_p1000_n100.json")))
+    p, n, tol = g["p"], g["n"], g["abs_tol"]
+    assert abs(sp.spmesl_lambda(sp.LAMBDA_UB, n, p) - g["lambda_ub"]) < tol
+    assert abs(sp.spmesl_lambda(sp.LAMBDA_PB, n, p) - g["lambda_pb"]) < tol
+    assert abs(sp.spmesl_lambda(sp.LAMBDA_UNIV_PM1, n, p) - g["lambda_univ_pm1"]) < tol
+    assert abs(sp.spmesl_lambda(sp.LAMBDA_UNIV, 50, 100) - math.sqrt(2 * math.log(100) / 50)) < 1e-15
+    assert math.isnan(sp.spmesl_lambda(sp.LAMBDA_GIVEN, n, p))
+
+
+def test_workspace_sizes():
+    for prec, s in ((sp.FP64, 8), (sp.FP32, 4)):
+        nb = sp.spmesl_fit_workspace_bytes(2000, prec)
+        assert nb >= 3 * 2000 * 2016 * s
+        assert sp.spmesl_solve_workspace_bytes(200, 2000, prec) > nb
+    assert sp.spmesl_fit_workspace_bytes(1, sp.FP32) == 0
+    assert sp.spmesl_max_p(sp.FP32) >= 10000
+    assert sp.spmesl_max_p(sp.FP64) >= 5000
+
+
+def test_invalid_arguments_rejected_on_host():
+    # no device work is enqueued on these paths: validation comes first
+    st = sp.Stats()
+    o = sp.spmesl_default_opts()
+    fake = 1 << 20        # never dereferenced
+    assert sp.spmesl_fit(None, 10, 5, 0.1, 1e-6, 10, o, fake, fake, None, fake, 1 << 30, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_fit(fake, 10, 1, 0.1, 1e-6, 10, o, fake, fake, None, fake, 1 << 30, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_fit(fake, 10, 5, -0.1, 1e-6, 10, o, fake, fake, None, fake, 1 << 30, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_fit(fake, 10, 5, 0.1, 0.0, 10, o, fake, fake, None, fake, 1 << 30, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_fit(fake, 10, 5, 0.1, 1e-6, 0, o, fake, fake, None, fake, 1 << 30, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_fit(fake, 10, 5, 0.1, 1e-6, 10, o, fake, fake, None, fake, 16, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_fit(fake + 8, 10, 5, 0.1, 1e-6, 10, o, fake, fake, None, fake + 8, 1 << 30, 0) == sp.SPMESL_EINVAL
+    big = sp.spmesl_max_p(sp.FP32) + 32
+    assert sp.spmesl_fit(fake, 10, big, 0.1, 1e-6, 10, o, fake, fake, None, fake, 1 << 40, 0) == sp.SPMESL_EINVAL
+    o.inner_rule = 7
+    assert sp.spmesl_fit(fake, 10, 5, 0.1, 1e-6, 10, o, fake, fake, None, fake, 1 << 30, 0) == sp.SPMESL_EINVAL
+    o = sp.spmesl_default_opts()
+    o.lambda_rule = sp.LAMBDA_UNIV
+    assert sp.spmesl_fit(fake, 0, 5, 0.0, 1e-6, 10, o, fake, fake, None, fake, 1 << 30, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_gram(fake, 0, 5, 5, sp.FP32, 0, fake, 5, fake, 1 << 20, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_gram(fake, 4, 5, 3, sp.FP32, 0, fake, 5, fake, 1 << 20, 0) == sp.SPMESL_EINVAL
+    assert sp.spmesl_gram(fake, 4, 5, 5, 9, 0, fake, 5, fake, 1 << 20, 0) == sp.SPMESL_EINVAL

@@ -1,0 +1,187 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bar (from the workload definition): max|Theta_gpu - Theta_oracle| <=
+1e-4 * max|Theta_oracle| in the FP64 and FP32 modes, supports equal except
+entries below 1e-6 * max|Theta|.  The FP64 path is also held to a much tighter
+bound, since it runs the same arithmetic in the same precision."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from checks import compare_theta, kkt_residual
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2203_15031_gb300 as sp  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+REL = 1e-4
+
+
+def _gpu_fit(X, lam, tol, maxit, prec, inner=sp.INNER_COLUMN, standardize=True, center=False,
+             wpb=0):
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).to(DEV)
+    S = sp.gram(Xd, precision=prec, center=center)
+    T, sig, st, B = sp.fit(S, lam, tol=tol, maxit=maxit, precision=prec, inner_rule=inner,
+                           standardize=standardize, warps_per_block=wpb, return_B=True)
+    return S.cpu().numpy(), T.cpu().numpy(), sig.cpu().numpy(), st, B.cpu().numpy()
+
+
+def _oracle_fit(X, lam, tol, maxit, standardize=True, center=False):
+    S = oracle.gram(X.astype(np.float64), center=center)
+    return S, oracle.spmesl(S, lam, tol=tol, maxit=maxit, standardize=standardize, nthreads=0)
+
+
+def _assert_parity(T, ref, rel=REL):
+    res = compare_theta(T, ref["Theta"], ref["B"], ref["sigma"], rel=rel)
+    assert res["ok"], res
+    return res
+
+
+# ---------------------------------------------------------------------------- Gram
+@pytest.mark.parametrize("prec,dt,n,p", [("fp64", np.float64, 50, 100), ("fp64", np.float64, 33, 129),
+                                         ("fp32", np.float32, 200, 333), ("fp32", np.float32, 7, 64),
+                                         ("fp32", np.float32, 1, 3)])
+@pytest.mark.parametrize("center", [False, True])
+def test_gram_parity(prec, dt, n, p, center):
+    rng = np.random.default_rng(n * 1000 + p)
+    X = (rng.standard_normal((n, p)) + (0.5 if center else 0.0)).astype(dt)
+    S = sp.gram(torch.from_numpy(X).to(DEV), precision=prec, center=center).cpu().numpy()
+    ref = oracle.gram(X.astype(np.float64), center=center)
+    scale = np.max(np.abs(ref))
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(S - ref)) <= tol * scale * max(1, n) ** 0.5
+    assert np.array_equal(S, S.T)
+
+
+# ---------------------------------------------------------------------------- small fits
+@pytest.mark.parametrize("inner", [sp.INNER_COLUMN, sp.INNER_JOINT])
+def test_ar1_p100_n50_fp64(inner):
+    w = synth.WORKLOADS["ar1_p100_n50_fp64"]
+    prob = synth.make_problem("ar1", 100, 50, 0, dtype=np.float64)
+    lam = prob.lambda0
+    assert abs(lam - math.sqrt(2 * math.log(100) / 50)) < 1e-15
+    S, T, sig, st, B = _gpu_fit(prob.X, lam, w["tol"], w["maxit"], "fp64", inner=inner)
+    Sref, ref = _oracle_fit(prob.X, lam, w["tol"], w["maxit"])
+    np.testing.assert_allclose(S, Sref, rtol=0, atol=1e-13 * np.abs(Sref).max())
+    assert st["status"] == sp.SPMESL_OK
+    res = _assert_parity(T, ref)
+    # same arithmetic in FP64: far inside the bar
+    assert res["max_rel_err"] < 1e-6
+    np.testing.assert_allclose(sig, ref["sigma"], rtol=1e-7)
+    viol, sig_err = kkt_residual(Sref, B, sig, lam)
+    assert viol < 1e-6 and sig_err < 1e-8
+
+
+@pytest.mark.parametrize("p,n,kind,prec,standardize", [
+    (37, 20, "er", "fp64", True), (75, 40, "hub_scaled", "fp32", True),
+    (130, 64, "er", "fp32", False), (200, 90, "ar1", "fp32", True),
+    (96, 50, "er", "fp64", False)])
+@pytest.mark.parametrize("inner", [sp.INNER_COLUMN, sp.INNER_JOINT])
+def test_small_fits_ragged_sizes(p, n, kind, prec, standardize, inner):
+    dt = np.float64 if prec == "fp64" else np.float32
+    prob = synth.make_problem(kind, p, n, p + n, dtype=dt)
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    _, T, sig, st, B = _gpu_fit(prob.X, prob.lambda0, tol, 2000, prec, inner=inner,
+                                standardize=standardize)
+    _, ref = _oracle_fit(prob.X, prob.lambda0, tol, 2000, standardize=standardize)
+    assert st["status"] == sp.SPMESL_OK, st
+    _assert_parity(T, ref)
+    assert np.array_equal(T, T.T)
+
+
+def test_warps_per_block_does_not_change_result():
+    prob = synth.make_problem("er", 160, 80, 5, dtype=np.float32)
+    outs = [_gpu_fit(prob.X, prob.lambda0, 1e-6, 1000, "fp32", wpb=w)[1] for w in (1, 3, 16)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_deterministic_repeat():
+    prob = synth.make_problem("hub_scaled", 180, 70, 9, dtype=np.float32)
+    a = _gpu_fit(prob.X, prob.lambda0, 1e-6, 1000, "fp32", inner=sp.INNER_JOINT)[1]
+    b = _gpu_fit(prob.X, prob.lambda0, 1e-6, 1000, "fp32", inner=sp.INNER_JOINT)[1]
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------- edge cases
+def test_p2_closed_form():
+    rho, lam = 0.7, 0.3
+    S = torch.tensor([[1.0, rho], [rho, 1.0]], dtype=torch.float64, device=DEV)
+    T, sig, st = sp.fit(S, lam, tol=1e-14, maxit=100000, precision="fp64")
+    sig2 = (1 - rho ** 2) / (1 - lam ** 2)
+    beta = rho - lam * math.sqrt(sig2)
+    want = np.array([[1 / sig2, -beta / sig2], [-beta / sig2, 1 / sig2]])
+    np.testing.assert_allclose(T.cpu().numpy(), want, rtol=1e-12)
+
+
+def test_identity_and_zero_solution():
+    T, sig, st = sp.fit(torch.eye(33, dtype=torch.float32, device=DEV), 0.1, precision="fp32")
+    np.testing.assert_array_equal(T.cpu().numpy(), np.eye(33))
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((40, 12)) * np.linspace(0.5, 3, 12)
+    S = X.T @ X / 40
+    SC, _ = oracle.standardize(S)
+    lam = np.abs(SC - np.diag(np.diag(SC))).max() * 1.001
+    T, sig, st = sp.fit(torch.from_numpy(S).to(DEV), lam, precision="fp64")
+    np.testing.assert_allclose(T.cpu().numpy(), np.diag(1 / np.diag(S)), rtol=1e-14)
+    assert st["nnz_B"] == 0
+
+
+def test_nonfinite_input_reported():
+    S = torch.eye(8, dtype=torch.float32, device=DEV)
+    S[3, 5] = float("nan")
+    with pytest.raises(sp.SpmeslError) as e:
+        sp.fit(S, 0.1, precision="fp32")
+    assert e.value.status == sp.SPMESL_ENONFINITE
+    S = torch.eye(8, dtype=torch.float64, device=DEV)
+    S[2, 2] = 0.0
+    with pytest.raises(sp.SpmeslError) as e:
+        sp.fit(S, 0.1, precision="fp64")
+    assert e.value.status == sp.SPMESL_ENONFINITE
+
+
+def test_iteration_cap_reports_not_converged():
+    prob = synth.make_problem("er", 64, 30, 2, dtype=np.float64)
+    S = torch.from_numpy(oracle.gram(prob.X)).to(DEV)
+    for inner in (sp.INNER_COLUMN, sp.INNER_JOINT):
+        T, sig, st = sp.fit(S, prob.lambda0, tol=1e-14, maxit=1, precision="fp64", inner_rule=inner)
+        assert st["status"] == sp.SPMESL_NOT_CONVERGED
+
+
+def test_degenerate_fit_flagged():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((4, 10))
+    S = torch.from_numpy(X.T @ X / 4).to(DEV)
+    with pytest.raises(sp.SpmeslError) as e:
+        sp.fit(S, 1e-7, tol=1e-9, maxit=300, precision="fp64")
+    assert e.value.status == sp.SPMESL_EDEGENERATE
+
+
+# ---------------------------------------------------------------------------- end to end
+def test_solve_from_host_matches_device_path():
+    prob = synth.make_problem("er", 300, 120, 4, dtype=np.float32)
+    Th, sh, st = sp.solve(prob.X, prob.lambda0, tol=1e-6, precision="fp32")
+    _, Td, sd, _, _ = _gpu_fit(prob.X, prob.lambda0, 1e-6, 1000, "fp32")
+    assert np.array_equal(Th, Td) and np.array_equal(sh, sd)
+    assert st["ms_fit"] > 0 and st["ms_gram"] > 0
+
+
+# ---------------------------------------------------------------------------- full size
+def test_er_p2000_n200_fp32_full():
+    w = synth.WORKLOADS["er_p2000_n200_fp32"]
+    prob = synth.make_problem("er", 2000, 200, 0, dtype=np.float32)
+    for inner in (sp.INNER_COLUMN, sp.INNER_JOINT):
+        _, T, sig, st, B = _gpu_fit(prob.X, prob.lambda0, w["tol"], w["maxit"], "fp32", inner=inner)
+        assert st["status"] == sp.SPMESL_OK, st
+        if inner == sp.INNER_COLUMN:
+            Sref, ref = _oracle_fit(prob.X, prob.lambda0, w["tol"], w["maxit"])
+        _assert_parity(T, ref)
