@@ -102,7 +102,9 @@ typedef struct {
     float ms_fit;               /* device time of the whole fit, ms */
     float ms_cd;                /* coordinate-descent kernel alone (record_phase_times), ms */
     float ms_theta;             /* Theta assembly kernel alone (record_phase_times), ms */
-    int64_t reserved[3];
+    int32_t max_col_sweeps;     /* largest number of sweeps any one column ran */
+    int32_t max_col_outer;      /* largest number of sigma iterations any one column ran */
+    int64_t reserved[2];
 } spmesl_stats;
 
 /* Fill `opts` with the defaults: FP32, standardize = 1, center = 0,

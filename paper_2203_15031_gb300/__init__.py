@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("n_degenerate", ctypes.c_int32), ("max_db", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("ms_gram", ctypes.c_float),
                 ("ms_fit", ctypes.c_float), ("ms_cd", ctypes.c_float),
-                ("ms_theta", ctypes.c_float), ("reserved", ctypes.c_int64 * 3)]
+                ("ms_theta", ctypes.c_float), ("max_col_sweeps", ctypes.c_int32),
+                ("max_col_outer", ctypes.c_int32), ("reserved", ctypes.c_int64 * 2)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -247,6 +247,8 @@ spmesl_status spmesl_fit_result(const void* workspace, int p, int precision, spm
         double md;
         memcpy(&md, &c.max_db_bits, sizeof(md));
         stats->max_db = md;
+        stats->max_col_sweeps = c.max_col_sweeps;
+        stats->max_col_outer = c.outer_max;
         read_phase_times(workspace, stats);
     }
     return s;

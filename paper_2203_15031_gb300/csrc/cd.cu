@@ -116,40 +116,79 @@ __device__ __forceinline__ void axpy_row(T* __restrict__ g, const T* __restrict_
 // One cyclic ascending sweep over k != j for column j (Algorithm 1's inner
 // loop, written on g = S_.j - S b).  Returns max |delta b| over the sweep
 // (same value in every lane); `moves` counts coordinates that changed.
+// Four consecutive elements starting at a 4-aligned index (16-byte or 2 x
+// 16-byte shared-memory loads).
+template <typename T>
+__device__ __forceinline__ void load4(const T* __restrict__ src, T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(src);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 q0 = *reinterpret_cast<const double2*>(src);
+        const double2 q1 = *reinterpret_cast<const double2*>(src + 2);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+}
+
+// Each lane evaluates 4 consecutive coordinates, so one step of the warp
+// covers 128 coordinates; the first coordinate whose update changes b is
+// applied and the scan resumes right after it.
+constexpr int SCAN_V = 4;
+
 template <typename T, bool STD>
 __device__ T sweep_column(int j, T* __restrict__ g, T* __restrict__ b, const CDArgs<T>& a, T lam,
                           unsigned long long& moves) {
     const int lane = threadIdx.x & 31;
     const int p = a.p;
+    const int ldp = a.ldp;
     T maxd = T(0);
     int cursor = 0;
     while (cursor < p) {
-        const int k = cursor + lane;
-        T bk = T(0), nb = T(0);
-        bool mv = false;
-        if (k < p && k != j) {
-            bk = b[k];
-            if constexpr (STD) {
-                nb = soft<T>(g[k] + bk, lam);                 // S_kk = 1
-            } else {
-                const T skk = a.diag[k];
-                nb = soft<T>(g[k] + skk * bk, lam) / skk;     // Soft(c, lambda)/S_kk
-            }
-            mv = (nb != bk);
+        const int base = cursor & ~(SCAN_V - 1);
+        const int k0 = base + lane * SCAN_V;
+        T gv[SCAN_V], bv[SCAN_V], nbv[SCAN_V];
+        if (k0 < ldp) {                       // ldp is a multiple of 32: the whole quad is in range
+            load4<T>(g + k0, gv);
+            load4<T>(b + k0, bv);
+        } else {
+#pragma unroll
+            for (int t = 0; t < SCAN_V; ++t) gv[t] = bv[t] = T(0);
         }
-        const unsigned bal = __ballot_sync(FULL_MASK, mv);
+        unsigned mvmask = 0u;
+#pragma unroll
+        for (int t = 0; t < SCAN_V; ++t) {
+            const int k = k0 + t;
+            nbv[t] = bv[t];
+            if (k >= cursor && k < p && k != j) {
+                T nb;
+                if constexpr (STD) {
+                    nb = soft<T>(gv[t] + bv[t], lam);                  // S_kk = 1
+                } else {
+                    const T skk = a.diag[k];
+                    nb = soft<T>(gv[t] + skk * bv[t], lam) / skk;      // Soft(c, lambda)/S_kk
+                }
+                nbv[t] = nb;
+                if (nb != bv[t]) mvmask |= 1u << t;
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL_MASK, mvmask != 0u);
         if (bal == 0u) {
-            cursor += 32;
+            cursor = base + 32 * SCAN_V;
             continue;
         }
         const int f = __ffs(bal) - 1;
-        const int ks = cursor + f;
-        const T nbs = __shfl_sync(FULL_MASK, nb, f);
-        const T delta = nbs - __shfl_sync(FULL_MASK, bk, f);
+        const int tf = __ffs(__shfl_sync(FULL_MASK, mvmask, f)) - 1;
+        T nb_sel = nbv[0], b_sel = bv[0];
+#pragma unroll
+        for (int t = 1; t < SCAN_V; ++t)
+            if (t == tf) { nb_sel = nbv[t]; b_sel = bv[t]; }
+        const T nbs = __shfl_sync(FULL_MASK, nb_sel, f);
+        const T delta = nbs - __shfl_sync(FULL_MASK, b_sel, f);
+        const int ks = base + f * SCAN_V + tf;
         if (lane == 0) b[ks] = nbs;
         maxd = fmax(maxd, fabs(delta));
         ++moves;
-        axpy_row<T>(g, a.SC + (size_t)ks * a.ldp, delta, a.ldp);
+        axpy_row<T>(g, a.SC + (size_t)ks * ldp, delta, ldp);
         __syncwarp();
         cursor = ks + 1;
     }
@@ -158,11 +197,49 @@ __device__ T sweep_column(int j, T* __restrict__ g, T* __restrict__ b, const CDA
 
 // sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the support of b
 // (Eq. (14) written on S).  Same value in every lane.
+// Per-warp scratch for the support list used by the sigma update.
+constexpr int SUPP_CAP = 128;
+
+// Shared memory of one warp: g_j and b_j (ldp elements each) and the list.
 template <typename T>
-__device__ double residual_quadratic_form(int j, const T* __restrict__ b, const CDArgs<T>& a) {
+__host__ __device__ constexpr size_t warp_smem_bytes(int ldp) {
+    return 2 * (size_t)ldp * sizeof(T) + SUPP_CAP * sizeof(int);
+}
+
+template <typename T>
+__device__ double residual_quadratic_form(int j, const T* __restrict__ b, const CDArgs<T>& a,
+                                          int* __restrict__ list) {
     const int lane = threadIdx.x & 31;
     const int p = a.p;
+    // support of b in ascending order
+    int ns = 0;
+    for (int c0 = 0; c0 < p; c0 += 32) {
+        const int k = c0 + lane;
+        const bool nz = k < p && b[k] != T(0);
+        const unsigned bal = __ballot_sync(FULL_MASK, nz);
+        if (nz) {
+            const int pos = ns + __popc(bal & ((1u << lane) - 1u));
+            if (pos < SUPP_CAP) list[pos] = k;
+        }
+        ns += __popc(bal);
+    }
+    __syncwarp();
     double lin = 0.0, quad = 0.0;
+    if (ns <= SUPP_CAP) {
+        for (int t = lane; t < ns; t += 32) {
+            const int k = list[t];
+            lin += (double)b[k] * (double)a.SC[(size_t)k * a.ldp + j];
+        }
+        for (int t = lane; t < ns * ns; t += 32) {
+            const int k = list[t / ns], l = list[t % ns];
+            quad += (double)b[k] * (double)b[l] * (double)a.SC[(size_t)k * a.ldp + l];
+        }
+        lin = warp_sum(lin);
+        quad = warp_sum(quad);
+        __syncwarp();
+        return (double)a.SC[(size_t)j * a.ldp + j] - 2.0 * lin + quad;
+    }
+    // large support: row-wise accumulation without the list
     for (int c0 = 0; c0 < p; c0 += 32) {
         const int k = c0 + lane;
         const T bk = (k < p) ? b[k] : T(0);
@@ -196,13 +273,14 @@ __global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    T* g = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * a.ldp;
+    T* g = reinterpret_cast<T*>(smem_raw + (size_t)warp * warp_smem_bytes<T>(a.ldp));
     T* b = g + a.ldp;
+    int* list = reinterpret_cast<int*>(b + a.ldp);
     FitCtrl* ctrl = a.ctrl;
     if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
 
     unsigned long long sweeps = 0, moves = 0;
-    int outer_max = 0, n_nc = 0, n_deg = 0;
+    int outer_max = 0, n_nc = 0, n_deg = 0, max_sw = 0;
     for (;;) {
         int j = 0;
         if (lane == 0) j = atomicAdd(&ctrl->next_col, 1);
@@ -214,6 +292,7 @@ __global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a) {
         __syncwarp();
 
         double sigma = 1.0;                                  // sigma^(0) = 1
+        const unsigned long long sweeps0 = sweeps;
         const double floor2 = 1e-12 * (double)a.SC[(size_t)j * a.ldp + j];
         int status = COL_OK;
         int r;
@@ -229,7 +308,7 @@ __global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a) {
                 }
             }
             if (!inner_ok) status |= COL_NOT_CONVERGED;
-            double q = residual_quadratic_form<T>(j, b, a);
+            double q = residual_quadratic_form<T>(j, b, a, list);
             if (q <= floor2) {
                 q = floor2;
                 status |= COL_DEGENERATE;
@@ -249,6 +328,7 @@ __global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a) {
             a.col_status[j] = status;
         }
         outer_max = max(outer_max, r + 1);
+        max_sw = max(max_sw, (int)(sweeps - sweeps0));
         n_nc += (status & COL_NOT_CONVERGED) != 0;
         n_deg += (status & COL_DEGENERATE) != 0;
         __syncwarp();
@@ -257,6 +337,7 @@ __global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a) {
         atomicAdd(&ctrl->total_sweeps, sweeps);
         atomicAdd(&ctrl->moves, moves);
         atomicMax(&ctrl->outer_max, outer_max);
+        atomicMax(&ctrl->max_col_sweeps, max_sw);
         if (n_nc) atomicAdd(&ctrl->n_not_converged, n_nc);
         if (n_deg) atomicAdd(&ctrl->n_degenerate, n_deg);
     }
@@ -343,8 +424,9 @@ __global__ void __launch_bounds__(512) cd_joint_kernel(CDArgs<T> a) {
     const int W = blockDim.x >> 5;
     const int gw = blockIdx.x * W + warp;
     const int TW = gridDim.x * W;
-    T* g = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * a.ldp;
+    T* g = reinterpret_cast<T*>(smem_raw + (size_t)warp * warp_smem_bytes<T>(a.ldp));
     T* b = g + a.ldp;
+    int* list = reinterpret_cast<int*>(b + a.ldp);
     FitCtrl* ctrl = a.ctrl;
     if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
 
@@ -404,7 +486,7 @@ __global__ void __launch_bounds__(512) cd_joint_kernel(CDArgs<T> a) {
                 warp_copy<T>(b, a.BT + (size_t)j * a.ldp, a.ldp);
             }
             __syncwarp();
-            double q = residual_quadratic_form<T>(j, b, a);
+            double q = residual_quadratic_form<T>(j, b, a, list);
             const double floor2 = 1e-12 * (double)a.SC[(size_t)j * a.ldp + j];
             if (q <= floor2) {
                 q = floor2;
@@ -428,6 +510,7 @@ __global__ void __launch_bounds__(512) cd_joint_kernel(CDArgs<T> a) {
     if (lane == 0) atomicAdd(&ctrl->moves, moves);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->total_sweeps = gs;
+        ctrl->max_col_sweeps = (int)gs;
         ctrl->outer_max = r < a.maxit ? r : a.maxit;
         ctrl->max_db_bits = dbits(gmax);
         const int left = *reinterpret_cast<volatile int*>(&ctrl->n_active);
@@ -489,9 +572,24 @@ __global__ void theta_kernel(const T* __restrict__ BT, int p, int ldp,
                              double* __restrict__ Theta, double* __restrict__ sigma_out,
                              FitCtrl* ctrl) {
     __shared__ T tileA[32][33];   // tileA[kk][jj] = BT[k0+kk][j0+jj] = b_{j,k}
+    // 1/sigma^2 and c for the tile's 32 columns k and 32 rows j: FP64
+    // divisions are expensive on this part, so each block does 64 of them
+    // instead of one per element
+    __shared__ double inv_k[32], inv_j[32], c_k[32], c_j[32];
     if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
     const int j0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    if (ty < 2) {
+        const int i = (ty == 0 ? k0 : j0) + tx;
+        double inv = 0.0, c = 0.0;
+        if (i < p) {
+            const double s = sigma[i];
+            inv = 1.0 / (s * s);
+            c = cs[i];
+        }
+        if (ty == 0) { inv_k[tx] = inv; c_k[tx] = c; }
+        else { inv_j[tx] = inv; c_j[tx] = c; }
+    }
     for (int rr = ty; rr < 32; rr += 8) {
         const int k = k0 + rr, j = j0 + tx;
         tileA[rr][tx] = (k < p && j < p) ? BT[(size_t)k * ldp + j] : T(0);
@@ -503,20 +601,26 @@ __global__ void theta_kernel(const T* __restrict__ BT, int p, int ldp,
         const int j = j0 + rr;
         if (j >= p || k >= p) continue;
         double out;
-        const double sk2 = sigma[k] * sigma[k];
         if (j == k) {
-            out = 1.0 / sk2;
+            out = inv_k[tx];
         } else {
-            const double sj2 = sigma[j] * sigma[j];
             const T bjk = tileA[tx][rr];                       // coefficient of x_j in regression k
             const T bkj = BT[(size_t)j * ldp + k];             // coefficient of x_k in regression j
             nnz += (bkj != T(0));
-            const double ojk = -(double)bjk / sk2;             // Omega_1[j][k]
-            const double okj = -(double)bkj / sj2;             // Omega_1[k][j]
-            if (j < k) out = fabs(ojk) > fabs(okj) ? okj : ojk;
-            else out = fabs(okj) > fabs(ojk) ? ojk : okj;      // pair (k, j) with k < j
+            if (bjk == T(0) && bkj == T(0)) {
+                out = 0.0;                                     // both candidates are zero
+            } else {
+                const double ojk = -(double)bjk * inv_k[tx];   // Omega_1[j][k]
+                const double okj = -(double)bkj * inv_j[rr];   // Omega_1[k][j]
+                if (j < k) out = fabs(ojk) > fabs(okj) ? okj : ojk;
+                else out = fabs(okj) > fabs(ojk) ? ojk : okj;  // pair (k, j) with k < j
+                out *= c_j[rr] * c_k[tx];
+            }
         }
-        Theta[(size_t)j * p + k] = out * cs[j] * cs[k];
+        if (j == k) out *= c_j[rr] * c_k[tx];
+        // the scale (c_j c_k) is formed before it multiplies, so (j, k) and
+        // (k, j) get bit-identical values and the result is exactly symmetric
+        Theta[(size_t)j * p + k] = out;
     }
     if (blockIdx.y == 0 && ty == 0 && k < p) sigma_out[k] = sigma[k] / cs[k];
     // one atomic per warp
@@ -568,7 +672,7 @@ static size_t smem_budget() { return (size_t)g_max_smem_block - 1024; }
 int max_p_for(int precision) {
     // one warp needs g and b: 2 * ldp * s bytes; the opt-in block limit on
     // GB300 is 227 KB.
-    const size_t budget = 232448 - 1024;
+    const size_t budget = 232448 - 1024 - SUPP_CAP * sizeof(int);
     const size_t s = (size_t)elem_size(precision);
     int p = (int)(budget / (2 * s));
     return p / 32 * 32;
@@ -616,11 +720,16 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     // warps per block: spread columns over the SMs, bounded by shared memory
-    const size_t per_warp = 2ull * L.ldp * sizeof(T);
+    const size_t per_warp = warp_smem_bytes<T>(L.ldp);
     int wmax = (int)std::min<size_t>(16, smem_budget() / per_warp);
     if (wmax < 1) return cudaErrorInvalidValue;
+    // Automatic shape: one block per SM holding ceil(p / #SM) warps, but
+    // shared memory capped at about half of the SM so the rest of the unified
+    // L1 keeps the few S rows a long-running column re-reads every sweep.
+    const bool auto_shape = f.warps_per_block <= 0;
     int W = (f.p + g_num_sms - 1) / g_num_sms;
-    if (f.warps_per_block > 0) W = f.warps_per_block;
+    if (auto_shape) W = std::min(W, (int)std::max<size_t>(1, (smem_budget() / 2) / per_warp));
+    else W = f.warps_per_block;
     W = std::max(1, std::min(W, wmax));
     const size_t smem = per_warp * W;
     const int threads = 32 * W;
@@ -635,7 +744,7 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) !=
             cudaSuccess)
             return e;
-        per_sm = std::max(per_sm, 1);
+        per_sm = auto_shape ? 1 : std::max(per_sm, 1);
         const int grid = std::min((f.p + W - 1) / W, g_num_sms * per_sm);
         kern<<<grid, threads, smem, st>>>(a);
     } else {

@@ -38,7 +38,8 @@ struct FitCtrl {
     unsigned long long max_db_bits;    // joint rule: max|delta| of the last sweep (double bits)
     unsigned long long nnz;            // nonzero b at exit
     int inner_cap_hit;                 // joint rule: inner cap reached in some outer iteration
-    int pad[7];
+    int max_col_sweeps;                // largest per-column sweep count
+    int pad[6];
 };
 static_assert(sizeof(FitCtrl) <= 256, "FitCtrl must fit its 256-byte slot");
 
