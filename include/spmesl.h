@@ -180,6 +180,32 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
                          const spmesl_opts* opts, double* Theta, double* sigma,
                          spmesl_stats* stats, void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * spmesl_fit without any device allocation and without a caller workspace.
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc or give the library scratch memory (for example a plugin whose
+ * host application owns all device memory, or real-time code that forbids
+ * allocation after start-up).
+ *   Arguments, outputs and device-side status are those of spmesl_fit, except
+ *   that there is no workspace: the fit's scratch is one 64 MiB __device__
+ *   array inside the library, held by every GPU that loads the library until
+ *   the process exits.  record_phase_times is ignored.
+ *   Size limit: the fit's scratch must fit in 64 MiB, i.e. p <= 2358 for
+ *   SPMESL_FP32 / SPMESL_MIXED and p <= 1664 for SPMESL_FP64; larger p returns
+ *   SPMESL_ENOMEM before any work is enqueued.
+ *   The first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents (each fit
+ *   clears what must start at zero).  Calls whose work overlaps on the GPU
+ *   race on the array: issue them on one stream or order them.
+ *   stats non-NULL synchronises `stream` and fills everything except the
+ *   timing fields.  No cudaMalloc, cudaFree or allocating library routine is
+ *   called.
+ */
+spmesl_status spmesl_fit_noalloc(const void* S, int n, int p, double lambda0, double tol,
+                                 int maxit, const spmesl_opts* opts, double* Theta, double* sigma,
+                                 spmesl_stats* stats, void* stream);
+
 /* Synchronise `stream` and read the status and counters of the last fit that
  * ran in `workspace` (p and precision as given to spmesl_fit).  Returns the
  * fit's status. */

@@ -24,7 +24,8 @@ __all__ = [
     "FP64", "FP32", "MIXED", "Opts", "Stats", "SpmeslError", "lib", "build",
     "spmesl_default_opts", "spmesl_status_string", "spmesl_version", "spmesl_lambda",
     "spmesl_max_p", "spmesl_gram_workspace_bytes", "spmesl_gram", "spmesl_fit_workspace_bytes",
-    "spmesl_fit", "spmesl_fit_result", "spmesl_fit_coefficients", "spmesl_solve_workspace_bytes",
+    "spmesl_fit", "spmesl_fit_noalloc", "spmesl_fit_result", "spmesl_fit_coefficients",
+    "spmesl_solve_workspace_bytes",
     "spmesl_solve", "gram", "fit", "solve",
 ]
 
@@ -78,6 +79,8 @@ _SIGS = {
     "spmesl_fit_workspace_bytes": (_sz, [_i32, _i32]),
     "spmesl_fit": (_i32, [_vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts), _vp, _vp,
                           ctypes.POINTER(Stats), _vp, _sz, _vp]),
+    "spmesl_fit_noalloc": (_i32, [_vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts), _vp,
+                                  _vp, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_result": (_i32, [_vp, _i32, _i32, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_coefficients": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "spmesl_solve_workspace_bytes": (_sz, [_i32, _i32, _i32]),
@@ -188,6 +191,16 @@ def spmesl_fit(S, n, p, lambda0, tol, maxit, opts, Theta, sigma, stats, workspac
                             ctypes.byref(opts) if opts is not None else None, _ptr(Theta),
                             _ptr(sigma), ctypes.byref(stats) if stats is not None else None,
                             _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def spmesl_fit_noalloc(S, n, p, lambda0, tol, maxit, opts, Theta, sigma, stats,
+                       stream=None) -> int:
+    """spmesl_fit for callers that cannot allocate device memory: the
+    library's own fixed 64 MiB device scratch replaces the workspace."""
+    return lib().spmesl_fit_noalloc(_ptr(S), n, p, lambda0, tol, maxit,
+                                    ctypes.byref(opts) if opts is not None else None, _ptr(Theta),
+                                    _ptr(sigma), ctypes.byref(stats) if stats is not None else None,
+                                    _stream(stream))
 
 
 def spmesl_fit_result(workspace, p, precision, stats, stream=None) -> int:
