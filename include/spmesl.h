@@ -85,7 +85,9 @@ typedef struct {
     int32_t warps_per_block;    /* 0 = chosen from p and shared-memory capacity */
     int32_t record_phase_times; /* 1: record CUDA events around the fit's phases on `stream`;
                                    spmesl_fit_result then fills ms_cd and ms_theta */
-    int32_t reserved[9];
+    int32_t use_graph;          /* spmesl_batch_run: capture the batch's launches once into a
+                                   CUDA graph and replay it on later runs */
+    int32_t reserved[8];
 } spmesl_opts;
 
 typedef struct {
@@ -232,6 +234,67 @@ spmesl_status spmesl_solve(const void* X_host, int n, int p, double lambda0, dou
                            int maxit, const spmesl_opts* opts, double* Theta_host,
                            double* sigma_host, spmesl_stats* stats, void* workspace,
                            size_t ws_bytes, void* stream);
+
+/*
+ * Batched fits: many independent SPMESL problems of different p and n solved
+ * together (Algorithm 2 for each; the columns of all fits share one
+ * coordinate-descent launch, Section 3.3's observation that the p column
+ * problems are independent extended across problems).
+ *
+ * spmesl_problem describes one fit; all pointers are device pointers owned by
+ * the caller and must stay valid while the batch runs:
+ *   X        n x p data (row-major, ld p) from which S = X'X/n is built, or
+ *            NULL to use S directly.  Element type per opts->precision.
+ *   S        p x p covariance (used when X is NULL).
+ *   lambda0  penalty level; <= 0 means "apply opts->lambda_rule with n, p".
+ *   Theta    p x p FP64 output; sigma p FP64 output (as spmesl_fit).
+ */
+typedef struct {
+    const void* X;
+    const void* S;
+    int32_t n;
+    int32_t p;
+    double lambda0;
+    double* Theta;
+    double* sigma;
+} spmesl_problem;
+
+typedef struct spmesl_batch spmesl_batch;
+
+/* Plan a batch (host only: sizes, ordering, workspace layout).  The problems
+ * are copied; tol and maxit apply to every fit.  opts: precision FP64 or FP32,
+ * inner_rule must be SPMESL_INNER_COLUMN, standardize / center / lambda_rule /
+ * warps_per_block / use_graph as documented in spmesl_opts.
+ * Errors: EINVAL (no problems, p < 2 or above spmesl_max_p, missing
+ * pointers, no usable lambda0), ENOMEM (host allocation). */
+spmesl_status spmesl_batch_create(const spmesl_problem* problems, int count, double tol,
+                                  int maxit, const spmesl_opts* opts, spmesl_batch** batch);
+
+/* Device workspace the batch needs (256-byte aligned when passed). */
+size_t spmesl_batch_workspace_bytes(const spmesl_batch* batch);
+
+/* Enqueue the whole batch on `stream`: descriptor upload, Gram (fits with X),
+ * standardisation, coordinate descent, Theta.  Asynchronous.  With use_graph
+ * the sequence is captured into a CUDA graph on the first run (per
+ * workspace) and replayed afterwards.  The workspace must not be reused until
+ * the run has completed. */
+spmesl_status spmesl_batch_run(spmesl_batch* batch, void* workspace, size_t ws_bytes,
+                               void* stream);
+
+/* Synchronise `stream`, write each fit's status to statuses[i] (host array in
+ * the caller's problem order, may be NULL) and aggregate counters to stats
+ * (may be NULL).  Returns the most severe status. */
+spmesl_status spmesl_batch_result(const spmesl_batch* batch, const void* workspace,
+                                  int32_t* statuses, spmesl_stats* stats, void* stream);
+
+/* Autotune warps per block of the batch's coordinate-descent launch by timing
+ * a few candidates on this workspace (runs the batch several times); the
+ * choice is kept in the batch and written to *best_warps. */
+spmesl_status spmesl_batch_tune(spmesl_batch* batch, void* workspace, size_t ws_bytes,
+                                void* stream, int* best_warps);
+
+/* Release the batch's host resources (pinned staging, captured graph). */
+void spmesl_batch_destroy(spmesl_batch* batch);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,9 @@ __all__ = [
     "spmesl_max_p", "spmesl_gram_workspace_bytes", "spmesl_gram", "spmesl_fit_workspace_bytes",
     "spmesl_fit", "spmesl_fit_noalloc", "spmesl_fit_result", "spmesl_fit_coefficients",
     "spmesl_solve_workspace_bytes",
-    "spmesl_solve", "gram", "fit", "solve",
+    "spmesl_solve", "spmesl_batch_create", "spmesl_batch_workspace_bytes", "spmesl_batch_run",
+    "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_destroy", "Problem", "Batch",
+    "gram", "fit", "solve",
 ]
 
 SPMESL_OK, SPMESL_NOT_CONVERGED = 0, 1
@@ -42,7 +44,14 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("standardize", ctypes.c_int32),
                 ("center", ctypes.c_int32), ("lambda_rule", ctypes.c_int32),
                 ("inner_rule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("record_phase_times", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("record_phase_times", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("S", ctypes.c_void_p), ("n", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("lambda0", ctypes.c_double), ("Theta", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -83,6 +92,14 @@ _SIGS = {
                                   _vp, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_result": (_i32, [_vp, _i32, _i32, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_coefficients": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "spmesl_batch_create": (_i32, [ctypes.POINTER(Problem), _i32, _dbl, _i32,
+                                   ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "spmesl_batch_workspace_bytes": (_sz, [_vp]),
+    "spmesl_batch_run": (_i32, [_vp, _vp, _sz, _vp]),
+    "spmesl_batch_result": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(Stats), _vp]),
+    "spmesl_batch_tune": (_i32, [_vp, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "spmesl_batch_destroy": (None, [_vp]),
     "spmesl_solve_workspace_bytes": (_sz, [_i32, _i32, _i32]),
     "spmesl_solve": (_i32, [_vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts), _vp, _vp,
                             ctypes.POINTER(Stats), _vp, _sz, _vp]),
@@ -276,6 +293,106 @@ def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=Tru
         out.append(B)
     del keep
     return tuple(out)
+
+
+def spmesl_batch_create(problems, count, tol, maxit, opts):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().spmesl_batch_create(problems, count, tol, maxit,
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(h))
+    return rc, h.value
+
+
+def spmesl_batch_workspace_bytes(batch) -> int:
+    return lib().spmesl_batch_workspace_bytes(batch)
+
+
+def spmesl_batch_run(batch, workspace, ws_bytes, stream=None) -> int:
+    return lib().spmesl_batch_run(batch, _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def spmesl_batch_result(batch, workspace, statuses, stats, stream=None) -> int:
+    return lib().spmesl_batch_result(batch, _ptr(workspace), statuses,
+                                     ctypes.byref(stats) if stats is not None else None,
+                                     _stream(stream))
+
+
+def spmesl_batch_tune(batch, workspace, ws_bytes, stream=None) -> tuple[int, int]:
+    w = ctypes.c_int(0)
+    rc = lib().spmesl_batch_tune(batch, _ptr(workspace), ws_bytes, _stream(stream),
+                                 ctypes.byref(w))
+    return rc, w.value
+
+
+def spmesl_batch_destroy(batch) -> None:
+    lib().spmesl_batch_destroy(batch)
+
+
+class Batch:
+    """Owning wrapper of a batch handle, its workspace and its outputs.
+
+    ``inputs`` is a list of (tensor, lambda0) where the tensor is either the
+    n x p data X (``kind='X'``) or the p x p covariance S (``kind='S'``);
+    outputs ``Theta[i]`` / ``sigma[i]`` are allocated here."""
+
+    def __init__(self, inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000,
+                 use_graph=False, warps_per_block=0, center=False, device=None):
+        import torch
+        _require_cuda()
+        prec = _prec(precision)
+        self.count = len(inputs)
+        self.inputs = [t.contiguous() for t, _ in inputs]
+        dev = device or self.inputs[0].device
+        self.Theta, self.sigma = [], []
+        arr = (Problem * self.count)()
+        for i, (t, lam) in enumerate(zip(self.inputs, (l for _, l in inputs))):
+            if kind == "X":
+                n, p = t.shape
+            else:
+                p = t.shape[0]
+                n = 0
+            Th = torch.empty((p, p), dtype=torch.float64, device=dev)
+            sg = torch.empty(p, dtype=torch.float64, device=dev)
+            self.Theta.append(Th)
+            self.sigma.append(sg)
+            arr[i] = Problem(t.data_ptr() if kind == "X" else None,
+                             t.data_ptr() if kind == "S" else None, n, p, float(lam),
+                             Th.data_ptr(), sg.data_ptr())
+        opts = spmesl_default_opts()
+        opts.precision = prec
+        opts.use_graph = int(bool(use_graph))
+        opts.warps_per_block = int(warps_per_block)
+        opts.center = int(bool(center))
+        rc, self.handle = spmesl_batch_create(arr, self.count, tol, maxit, opts)
+        _check(rc, "spmesl_batch_create")
+        self.ws_bytes = spmesl_batch_workspace_bytes(self.handle)
+        self._keep, self.ws = _workspace(self.ws_bytes, dev)
+
+    def run(self, stream=None):
+        _check(spmesl_batch_run(self.handle, self.ws, self.ws_bytes, stream), "spmesl_batch_run")
+
+    def tune(self, stream=None) -> int:
+        rc, w = spmesl_batch_tune(self.handle, self.ws, self.ws_bytes, stream)
+        _check(rc, "spmesl_batch_tune")
+        return w
+
+    def result(self, stream=None):
+        st = Stats()
+        statuses = (ctypes.c_int32 * self.count)()
+        spmesl_batch_result(self.handle, self.ws, statuses, st, stream)
+        return list(statuses), st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spmesl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve(X_host, lambda0, tol=1e-6, maxit=1000, precision="fp32", center=False,

@@ -1,0 +1,576 @@
+// Batched SPMESL: many independent fits of different p and n in one pass of
+// four launches (Gram tiles, standardisation, coordinate descent, Theta).
+//
+// Every launch covers all fits at once.  Fits are ordered by decreasing p so
+// the longest column chains start first.  A descriptor table in the
+// workspace gives each fit its buffers and its first global column / tile
+// index; a block or warp finds its fit by binary search over those prefix
+// sums.  The coordinate-descent launch is one dynamic queue of all columns of
+// all fits (one warp per column, the same column solver as spmesl_fit), so a
+// fit's slow columns overlap with other fits' work instead of idling the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "cd_device.cuh"
+#include "gram_device.cuh"
+
+namespace spmesl {
+
+struct BatchFit {
+    const void* X;        // device data (n x p, ld p) or nullptr
+    const void* S;        // covariance the fit reads (user S or the Gram output)
+    void* Sg;             // Gram output in the workspace (when X is given)
+    void* mu;             // column means (centring)
+    void* SC;
+    void* BT;
+    void* diag;
+    double* cs;
+    double* sigma;
+    int* col_status;
+    double* Theta;
+    double* sigma_out;
+    FitCtrl* ctrl;
+    double lambda0;
+    int n, p, ldp;
+    int col_start, gram_start, theta_start;
+    int pad[2];
+};
+
+struct BatchHeader {
+    int next_col;
+    int pad[63];
+};
+
+// Largest f with prefix[f] <= idx (prefix ascending, prefix[0] = 0).
+__device__ __forceinline__ int find_fit(const int* __restrict__ prefix, int count, int idx) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void batch_mean_kernel(const BatchFit* __restrict__ fits) {
+    const BatchFit& f = fits[blockIdx.y];
+    if (!f.X || !f.mu) return;
+    column_means<T>(static_cast<const T*>(f.X), f.n, f.p, f.p, static_cast<T*>(f.mu),
+                    blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) batch_gram_kernel(const BatchFit* __restrict__ fits,
+                                                        const int* __restrict__ gram_prefix,
+                                                        int count) {
+    const int fi = find_fit(gram_prefix, count, blockIdx.x);
+    const BatchFit& f = fits[fi];
+    const int t = (f.p + GRAM_BM - 1) / GRAM_BM;
+    int tm, tn;
+    upper_tile(blockIdx.x - f.gram_start, t, tm, tn);
+    gram_tile<T>(static_cast<const T*>(f.X), f.n, f.p, f.p, static_cast<const T*>(f.mu),
+                 static_cast<T*>(f.Sg), f.p, (T)(1.0 / (double)f.n), tm, tn);
+}
+
+template <typename T>
+__global__ void batch_prep_diag_kernel(const BatchFit* __restrict__ fits, int standardize) {
+    const BatchFit& f = fits[blockIdx.y];
+    const T* S = static_cast<const T*>(f.S);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < f.p; j += gridDim.x * blockDim.x) {
+        const double d = (double)S[(size_t)j * f.p + j];
+        if (!(d > 0.0) || !isfinite(d)) set_error(f.ctrl, DEV_ERR_NONFINITE);
+        f.cs[j] = standardize ? 1.0 / sqrt(d) : 1.0;
+        f.sigma[j] = 1.0;
+        f.col_status[j] = COL_OK;
+    }
+}
+
+template <typename T>
+__global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits) {
+    const BatchFit& f = fits[blockIdx.y];
+    const T* S = static_cast<const T*>(f.S);
+    T* SC = static_cast<T*>(f.SC);
+    T* BT = static_cast<T*>(f.BT);
+    T* diag = static_cast<T*>(f.diag);
+    const size_t total = (size_t)f.p * f.ldp;
+    bool bad = false;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / f.ldp), c = (int)(i % f.ldp);
+        T v = T(0);
+        if (c < f.p) {
+            const T s = S[(size_t)r * f.p + c];
+            bad |= !isfinite((double)s);
+            v = (T)((double)s * f.cs[r] * f.cs[c]);
+            if (c == r) diag[r] = v;
+        }
+        SC[i] = v;
+        BT[i] = T(0);
+    }
+    if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
+}
+
+template <typename T, bool STD>
+__global__ void __launch_bounds__(512) batch_cd_kernel(const BatchFit* __restrict__ fits,
+                                                       const int* __restrict__ col_prefix,
+                                                       int count, int total_cols, int max_ldp,
+                                                       double tol, int maxit,
+                                                       BatchHeader* hdr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    T* g = reinterpret_cast<T*>(smem_raw + (size_t)warp * warp_smem_bytes<T>(max_ldp));
+    for (;;) {
+        int gc = 0;
+        if (lane == 0) gc = atomicAdd(&hdr->next_col, 1);
+        gc = __shfl_sync(FULL_MASK, gc, 0);
+        if (gc >= total_cols) break;
+        const int fi = find_fit(col_prefix, count, gc);
+        const BatchFit& f = fits[fi];
+        if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) continue;
+        CDArgs<T> a;
+        a.SC = static_cast<const T*>(f.SC);
+        a.BT = static_cast<T*>(f.BT);
+        a.GT = nullptr;
+        a.diag = static_cast<const T*>(f.diag);
+        a.sigma = f.sigma;
+        a.col_status = f.col_status;
+        a.active = a.active_next = a.flag = nullptr;
+        a.ctrl = f.ctrl;
+        a.p = f.p;
+        a.ldp = f.ldp;
+        a.maxit = maxit;
+        a.lambda0 = f.lambda0;
+        a.tol = tol;
+        T* b = g + f.ldp;
+        int* list = reinterpret_cast<int*>(b + f.ldp);
+        ColCounters cnt;
+        solve_column<T, STD>(gc - f.col_start, g, b, list, a, cnt);
+        flush_counters(f.ctrl, cnt);
+    }
+}
+
+template <typename T>
+__global__ void batch_theta_kernel(const BatchFit* __restrict__ fits,
+                                   const int* __restrict__ theta_prefix, int count) {
+    const int fi = find_fit(theta_prefix, count, blockIdx.x);
+    const BatchFit& f = fits[fi];
+    if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) return;
+    const int t = (f.p + 31) / 32;
+    const int idx = blockIdx.x - f.theta_start;
+    theta_tile<T>(static_cast<const T*>(f.BT), f.p, f.ldp, f.sigma, f.cs, f.Theta, f.sigma_out,
+                  f.ctrl, (idx / t) * 32, (idx % t) * 32);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FitPlan {
+    int src;                 // index in the caller's array
+    int n, p, ldp;
+    double lambda0;
+    const void* X;
+    const void* S;
+    double* Theta;
+    double* sigma;
+    size_t off_ctrl, off_cs, off_sigma, off_status, off_diag, off_mu, off_Sg, off_SC, off_BT;
+    int col_start, gram_start, theta_start;
+};
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+int max_smem_block() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    return v;
+}
+
+}  // namespace
+}  // namespace spmesl
+
+using namespace spmesl;
+
+struct spmesl_batch {
+    int count = 0;
+    int precision = SPMESL_FP32;
+    int standardize = 1;
+    int center = 0;
+    int use_graph = 0;
+    double tol = 1e-6;
+    int maxit = 1000;
+    int warps_per_block = 0;       // 0 = automatic
+    std::vector<FitPlan> plan;     // ordered by decreasing p
+    size_t off_hdr = 0, off_desc = 0, off_colp = 0, off_gramp = 0, off_thetap = 0, off_ctrls = 0;
+    size_t ws_bytes = 0;
+    int total_cols = 0, total_gram = 0, total_theta = 0, max_ldp = 32, max_p = 2, max_n = 1;
+    bool any_x = false;
+    // pinned staging of the descriptor table and the prefix arrays
+    unsigned char* pinned = nullptr;
+    size_t table_bytes = 0;
+    const void* table_ws = nullptr;    // workspace the staged table points into
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_ws = nullptr;
+    int graph_W = -1;
+    cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, int W) {
+    const BatchFit* fits = reinterpret_cast<const BatchFit*>(ws + b->off_desc);
+    const int* colp = reinterpret_cast<const int*>(ws + b->off_colp);
+    const int* gramp = reinterpret_cast<const int*>(ws + b->off_gramp);
+    const int* thetap = reinterpret_cast<const int*>(ws + b->off_thetap);
+    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(ws + b->off_hdr);
+    cudaError_t e;
+    // descriptor table + prefix arrays, then the control blocks and the queue
+    if ((e = cudaMemcpyAsync(ws + b->off_desc, b->pinned, b->table_bytes, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(ws + b->off_hdr, 0, sizeof(BatchHeader), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws + b->off_ctrls, 0, (size_t)256 * b->count, st)) != cudaSuccess)
+        return e;
+    const int count = b->count;
+    if (b->any_x) {
+        if (b->center)
+            batch_mean_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits);
+        batch_gram_kernel<T><<<b->total_gram, 256, 0, st>>>(fits, gramp, count);
+    }
+    batch_prep_diag_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits,
+                                                                                   b->standardize);
+    const int mx = std::max(1, std::min(64, (int)(((size_t)b->max_p * b->max_ldp + 8191) / 8192)));
+    batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits);
+
+    const size_t per_warp = warp_smem_bytes<T>(b->max_ldp);
+    const size_t budget = (size_t)max_smem_block() - 1024;
+    const int wmax = (int)std::min<size_t>(16, budget / per_warp);
+    if (wmax < 1) return cudaErrorInvalidValue;
+    W = std::max(1, std::min(W, wmax));
+    const size_t smem = per_warp * W;
+    auto kern = b->standardize ? batch_cd_kernel<T, true> : batch_cd_kernel<T, false>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * W, smem)) !=
+        cudaSuccess)
+        return e;
+    per_sm = std::max(per_sm, 1);
+    const int grid = std::min((b->total_cols + W - 1) / W, num_sms() * per_sm);
+    kern<<<grid, 32 * W, smem, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
+                                     b->maxit, hdr);
+    batch_theta_kernel<T><<<b->total_theta, dim3(32, 8), 0, st>>>(fits, thetap, count);
+    return cudaGetLastError();
+}
+
+// Default warps per block: fill every SM with enough warps for the columns,
+// keeping shared memory near half of the SM (see the single-fit launcher).
+int auto_warps(const spmesl_batch* b) {
+    const size_t per_warp = b->precision == SPMESL_FP64 ? warp_smem_bytes<double>(b->max_ldp)
+                                                        : warp_smem_bytes<float>(b->max_ldp);
+    const size_t budget = (size_t)max_smem_block() - 1024;
+    int W = (b->total_cols + num_sms() - 1) / num_sms();
+    W = std::min(W, (int)std::max<size_t>(1, (budget / 2) / per_warp));
+    return std::max(1, std::min(16, W));
+}
+
+// Fill the pinned table with device addresses inside `ws`.
+void stage_table(spmesl_batch* b, unsigned char* ws) {
+    BatchFit* t = reinterpret_cast<BatchFit*>(b->pinned);
+    int* colp = reinterpret_cast<int*>(b->pinned + (b->off_colp - b->off_desc));
+    int* gramp = reinterpret_cast<int*>(b->pinned + (b->off_gramp - b->off_desc));
+    int* thetap = reinterpret_cast<int*>(b->pinned + (b->off_thetap - b->off_desc));
+    for (int i = 0; i < b->count; ++i) {
+        const FitPlan& f = b->plan[i];
+        BatchFit d{};
+        d.X = f.X;
+        d.Sg = f.X ? ws + f.off_Sg : nullptr;
+        d.S = f.X ? d.Sg : f.S;
+        d.mu = (f.X && b->center) ? ws + f.off_mu : nullptr;
+        d.SC = ws + f.off_SC;
+        d.BT = ws + f.off_BT;
+        d.diag = ws + f.off_diag;
+        d.cs = reinterpret_cast<double*>(ws + f.off_cs);
+        d.sigma = reinterpret_cast<double*>(ws + f.off_sigma);
+        d.col_status = reinterpret_cast<int*>(ws + f.off_status);
+        d.Theta = f.Theta;
+        d.sigma_out = f.sigma;
+        d.ctrl = reinterpret_cast<FitCtrl*>(ws + f.off_ctrl);
+        d.lambda0 = f.lambda0;
+        d.n = f.n;
+        d.p = f.p;
+        d.ldp = f.ldp;
+        d.col_start = f.col_start;
+        d.gram_start = f.gram_start;
+        d.theta_start = f.theta_start;
+        t[i] = d;
+        colp[i] = f.col_start;
+        gramp[i] = f.gram_start;
+        thetap[i] = f.theta_start;
+    }
+    colp[b->count] = b->total_cols;
+    gramp[b->count] = b->total_gram;
+    thetap[b->count] = b->total_theta;
+    b->table_ws = ws;
+}
+
+spmesl_status status_of(const FitCtrl& c) {
+    if (c.err == DEV_ERR_NONFINITE) return SPMESL_ENONFINITE;
+    if (c.err == DEV_ERR_TIMEOUT) return SPMESL_ETIMEOUT;
+    if (c.n_degenerate > 0) return SPMESL_EDEGENERATE;
+    if (c.n_not_converged > 0) return SPMESL_NOT_CONVERGED;
+    return SPMESL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double tol, int maxit,
+                                  const spmesl_opts* opts, spmesl_batch** out) {
+    if (!out) return SPMESL_EINVAL;
+    *out = nullptr;
+    spmesl_opts o;
+    if (opts) o = *opts;
+    else spmesl_default_opts(&o);
+    if (!probs || count < 1 || !(tol > 0.0) || maxit < 1) return SPMESL_EINVAL;
+    if (o.precision != SPMESL_FP64 && o.precision != SPMESL_FP32) return SPMESL_EINVAL;
+    if (o.inner_rule != SPMESL_INNER_COLUMN) return SPMESL_EINVAL;
+    const int maxp = max_p_for(o.precision);
+    for (int i = 0; i < count; ++i) {
+        const spmesl_problem& q = probs[i];
+        if (q.p < 2 || q.p > maxp || !q.Theta || !q.sigma || (!q.X && !q.S)) return SPMESL_EINVAL;
+        if (q.X && q.n < 1) return SPMESL_EINVAL;
+        double lam = q.lambda0;
+        if (!(lam > 0.0)) lam = spmesl_lambda(o.lambda_rule, q.n, q.p);
+        if (!(lam > 0.0) || !isfinite(lam)) return SPMESL_EINVAL;
+    }
+    spmesl_batch* b = new (std::nothrow) spmesl_batch();
+    if (!b) return SPMESL_ENOMEM;
+    b->count = count;
+    b->precision = o.precision;
+    b->standardize = o.standardize ? 1 : 0;
+    b->center = o.center ? 1 : 0;
+    b->use_graph = o.use_graph ? 1 : 0;
+    b->warps_per_block = o.warps_per_block;
+    b->tol = tol;
+    b->maxit = maxit;
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return probs[a].p > probs[c].p; });
+    const size_t s = (size_t)elem_size(o.precision);
+    size_t off = 0;
+    b->off_hdr = off;   off += align_up(sizeof(BatchHeader), 256);
+    b->off_desc = off;  off += align_up(sizeof(BatchFit) * count, 256);
+    b->off_colp = off;  off += align_up(sizeof(int) * (count + 1), 256);
+    b->off_gramp = off; off += align_up(sizeof(int) * (count + 1), 256);
+    b->off_thetap = off; off += align_up(sizeof(int) * (count + 1), 256);
+    b->table_bytes = off - b->off_desc;
+    b->off_ctrls = off; off += (size_t)256 * count;      // one FitCtrl slot per fit
+    int cols = 0, gram = 0, theta = 0;
+    for (int k = 0; k < count; ++k) {
+        const spmesl_problem& q = probs[order[k]];
+        FitPlan f{};
+        f.src = order[k];
+        f.n = q.n;
+        f.p = q.p;
+        f.ldp = padded_ld(q.p);
+        f.lambda0 = q.lambda0 > 0.0 ? q.lambda0 : spmesl_lambda(o.lambda_rule, q.n, q.p);
+        f.X = q.X;
+        f.S = q.S;
+        f.Theta = q.Theta;
+        f.sigma = q.sigma;
+        const size_t mat = align_up((size_t)f.p * f.ldp * s, 256);
+        f.off_ctrl = b->off_ctrls + (size_t)256 * k;
+        f.off_cs = off;     off += align_up((size_t)f.p * 8, 256);
+        f.off_sigma = off;  off += align_up((size_t)f.p * 8, 256);
+        f.off_status = off; off += align_up((size_t)f.p * 4, 256);
+        f.off_diag = off;   off += align_up((size_t)f.p * s, 256);
+        if (q.X) {
+            f.off_mu = off;  off += align_up((size_t)f.p * s, 256);
+            f.off_Sg = off;  off += align_up((size_t)f.p * f.p * s, 256);
+            b->any_x = true;
+        }
+        f.off_SC = off;     off += mat;
+        f.off_BT = off;     off += mat;
+        f.col_start = cols;
+        cols += f.p;
+        f.gram_start = gram;
+        if (q.X) {
+            const int t = (f.p + GRAM_BM - 1) / GRAM_BM;
+            gram += t * (t + 1) / 2;
+        }
+        f.theta_start = theta;
+        const int tt = (f.p + 31) / 32;
+        theta += tt * tt;
+        b->max_ldp = std::max(b->max_ldp, f.ldp);
+        b->max_p = std::max(b->max_p, f.p);
+        b->max_n = std::max(b->max_n, f.n);
+        b->plan.push_back(f);
+    }
+    b->total_cols = cols;
+    b->total_gram = gram;
+    b->total_theta = theta;
+    b->ws_bytes = off;
+    if (cudaMallocHost(&b->pinned, b->table_bytes) != cudaSuccess) {
+        delete b;
+        return SPMESL_ENOMEM;
+    }
+    *out = b;
+    return SPMESL_OK;
+}
+
+size_t spmesl_batch_workspace_bytes(const spmesl_batch* b) { return b ? b->ws_bytes : 0; }
+
+spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes, void* stream) {
+    if (!b || !workspace || ws_bytes < b->ws_bytes) return SPMESL_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return SPMESL_EINVAL;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b->table_ws != workspace) {
+        // the staged table may still be read by an earlier copy on `st`
+        if (b->table_ws && cudaStreamSynchronize(st) != cudaSuccess) return SPMESL_ECUDA;
+        stage_table(b, ws);
+    }
+    const int W = b->warps_per_block > 0 ? b->warps_per_block : auto_warps(b);
+    auto enqueue = [&](cudaStream_t s2) {
+        return b->precision == SPMESL_FP64 ? enqueue_batch<double>(b, ws, s2, W)
+                                           : enqueue_batch<float>(b, ws, s2, W);
+    };
+    if (!b->use_graph) {
+        cudaError_t e = enqueue(st);
+        return e == cudaSuccess ? SPMESL_OK : SPMESL_ECUDA;
+    }
+    if (!b->graph || b->graph_ws != workspace || b->graph_W != W) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        if (!b->cap_stream &&
+            cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return SPMESL_ECUDA;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return SPMESL_ECUDA;
+        cudaError_t e = enqueue(b->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return SPMESL_ECUDA;
+        }
+        e = cudaGraphInstantiate(&b->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return SPMESL_ECUDA;
+        b->graph_ws = workspace;
+        b->graph_W = W;
+    }
+    return cudaGraphLaunch(b->graph, st) == cudaSuccess ? SPMESL_OK : SPMESL_ECUDA;
+}
+
+spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, int32_t* statuses,
+                                  spmesl_stats* stats, void* stream) {
+    if (!b || !workspace) return SPMESL_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SPMESL_ECUDA;
+    const unsigned char* ws = static_cast<const unsigned char*>(workspace);
+    std::vector<unsigned char> ctrls((size_t)256 * b->count);
+    if (cudaMemcpy(ctrls.data(), ws + b->off_ctrls, ctrls.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return SPMESL_ECUDA;
+    spmesl_status worst = SPMESL_OK;
+    spmesl_stats agg;
+    memset(&agg, 0, sizeof(agg));
+    for (const FitPlan& f : b->plan) {
+        FitCtrl c;
+        memcpy(&c, ctrls.data() + (f.off_ctrl - b->off_ctrls), sizeof(c));
+        const spmesl_status s = status_of(c);
+        if (statuses) statuses[f.src] = s;
+        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+        else if (s > 0 && worst == SPMESL_OK) worst = s;
+        agg.outer_iters = std::max(agg.outer_iters, c.outer_max);
+        agg.inner_sweeps += (int64_t)c.total_sweeps;
+        agg.moves += (int64_t)c.moves;
+        agg.nnz_B += (int64_t)c.nnz;
+        agg.n_not_converged += c.n_not_converged;
+        agg.n_degenerate += c.n_degenerate;
+        agg.max_col_sweeps = std::max(agg.max_col_sweeps, c.max_col_sweeps);
+        agg.max_col_outer = std::max(agg.max_col_outer, c.outer_max);
+    }
+    agg.status = worst;
+    if (stats) *stats = agg;
+    return worst;
+}
+
+spmesl_status spmesl_batch_tune(spmesl_batch* b, void* workspace, size_t ws_bytes, void* stream,
+                                int* best_warps) {
+    if (!b) return SPMESL_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int saved_graph = b->use_graph;
+    b->use_graph = 0;
+    static const int cand[] = {2, 4, 6, 8, 12, 16};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return SPMESL_ECUDA;
+    float best = 1e30f;
+    int bestW = auto_warps(b);
+    for (int W : cand) {
+        b->warps_per_block = W;
+        float tot = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaEventRecord(e0, st);
+            ok = spmesl_batch_run(b, workspace, ws_bytes, stream) == SPMESL_OK;
+            cudaEventRecord(e1, st);
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;           // first run warms up
+            } else {
+                ok = false;
+            }
+        }
+        if (ok && tot < best) {
+            best = tot;
+            bestW = W;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->warps_per_block = bestW;
+    b->use_graph = saved_graph;
+    if (best_warps) *best_warps = bestW;
+    return best < 1e29f ? SPMESL_OK : SPMESL_ECUDA;
+}
+
+void spmesl_batch_destroy(spmesl_batch* b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    delete b;
+}
+
+}  // extern "C"

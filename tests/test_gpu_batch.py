@@ -1,0 +1,122 @@
+"""Batched fits (many problems of different p and n per launch) through the C
+ABI: every fit in a batch must equal the same fit run alone, match the FP64
+oracle, and keep its own status."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from checks import compare_theta
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2203_15031_gb300 as sp  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def _single(X, lam, prec, tol, maxit=1000):
+    S = sp.gram(X, precision=prec)
+    T, sg, st = sp.fit(S, lam, tol=tol, maxit=maxit, precision=prec)
+    return T.cpu().numpy(), sg.cpu().numpy(), st
+
+
+def _problems(specs, dt):
+    probs = [synth.make_problem(s["kind"], s["p"], s["n"], s["seed"], dtype=dt) for s in specs]
+    return probs, [(torch.from_numpy(pr.X).to(DEV), pr.lambda0) for pr in probs]
+
+
+SMALL = [dict(kind="er", p=37, n=20, seed=1), dict(kind="ar1", p=200, n=90, seed=2),
+         dict(kind="hub_scaled", p=75, n=40, seed=3), dict(kind="er", p=130, n=64, seed=4),
+         dict(kind="ar1", p=2, n=10, seed=5), dict(kind="er", p=64, n=7, seed=6)]
+
+
+@pytest.mark.parametrize("prec,dt,tol", [("fp32", np.float32, 1e-6), ("fp64", np.float64, 1e-9)])
+def test_batch_equals_single_fits_and_oracle(prec, dt, tol):
+    probs, inputs = _problems(SMALL, dt)
+    bt = sp.Batch(inputs, kind="X", precision=prec, tol=tol)
+    bt.run()
+    statuses, st = bt.result()
+    assert all(s == sp.SPMESL_OK for s in statuses), statuses
+    for i, (pr, (X, lam)) in enumerate(zip(probs, inputs)):
+        T1, s1, _ = _single(X, lam, prec, tol)
+        Tb, sb = bt.Theta[i].cpu().numpy(), bt.sigma[i].cpu().numpy()
+        assert np.array_equal(Tb, T1) and np.array_equal(sb, s1), i
+        ref = oracle.spmesl(oracle.gram(pr.X.astype(np.float64)), lam, tol=tol, maxit=1000)
+        assert compare_theta(Tb, ref["Theta"], ref["B"], ref["sigma"])["ok"]
+    bt.close()
+
+
+def test_batch_from_covariances_and_graph_replay():
+    probs, inputs = _problems(SMALL[:4], np.float32)
+    Ss = [(sp.gram(X, precision="fp32"), lam) for X, lam in inputs]
+    plain = sp.Batch(Ss, kind="S", precision="fp32")
+    plain.run()
+    plain.result()
+    graphed = sp.Batch(Ss, kind="S", precision="fp32", use_graph=True)
+    for _ in range(3):                  # capture, then replays
+        graphed.run()
+        statuses, _ = graphed.result()
+        assert all(s == sp.SPMESL_OK for s in statuses)
+        for a, b in zip(plain.Theta, graphed.Theta):
+            assert torch.equal(a, b)
+    plain.close()
+    graphed.close()
+
+
+def test_bad_fit_keeps_its_error_to_itself():
+    probs, inputs = _problems(SMALL[:3], np.float32)
+    bad = inputs[1][0].clone()
+    bad[3, 5] = float("nan")
+    inputs[1] = (bad, inputs[1][1])
+    bt = sp.Batch(inputs, kind="X", precision="fp32")
+    bt.run()
+    statuses, _ = bt.result()
+    assert statuses[1] == sp.SPMESL_ENONFINITE
+    assert statuses[0] == sp.SPMESL_OK and statuses[2] == sp.SPMESL_OK
+    T0, _, _ = _single(inputs[0][0], inputs[0][1], "fp32", 1e-6)
+    assert np.array_equal(bt.Theta[0].cpu().numpy(), T0)
+    bt.close()
+
+
+def test_tuned_warps_do_not_change_results():
+    probs, inputs = _problems(SMALL, np.float32)
+    bt = sp.Batch(inputs, kind="X", precision="fp32")
+    bt.run()
+    bt.result()
+    before = [t.clone() for t in bt.Theta]
+    w = bt.tune()
+    assert 1 <= w <= 16
+    bt.run()
+    bt.result()
+    for a, b in zip(before, bt.Theta):
+        assert torch.equal(a, b)
+    bt.close()
+
+
+def test_mixed_batch_256_fits():
+    """256 fits, p log-uniform in [50, 2000], n uniform in [30, 400], networks
+    mixed; every fit equals its single-fit run and a sample matches the oracle."""
+    specs = synth.batch_specs(256)
+    probs, inputs = _problems(specs, np.float32)
+    bt = sp.Batch(inputs, kind="X", precision="fp32", use_graph=True)
+    bt.run()
+    statuses, st = bt.result()
+    assert all(s in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED) for s in statuses)
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(256, 12, replace=False).tolist())
+    for i, (pr, (X, lam)) in enumerate(zip(probs, inputs)):
+        T1, s1, _ = _single(X, lam, "fp32", 1e-6)
+        assert np.array_equal(bt.Theta[i].cpu().numpy(), T1), i
+        if i in sample:
+            ref = oracle.spmesl(oracle.gram(pr.X.astype(np.float64)), lam, tol=1e-6, maxit=1000,
+                                nthreads=0)
+            res = compare_theta(T1, ref["Theta"], ref["B"], ref["sigma"])
+            assert res["ok"], (i, res)
+    bt.close()
