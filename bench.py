@@ -3,9 +3,11 @@
 Workload (default): Erdos-Renyi network, p = 2000, n = 200, X float32 with
 rows N(0, Theta^{-1}), lambda0 = sqrt(2 log p / n), tol 1e-6, maxit 1000,
 FP32 Gram and FP32 coordinate descent (sigma and Theta in FP64).  One step is
-one whole SPMESL solve through the C ABI: Gram S = X'X/n, standardisation,
-coordinate descent with sigma updates, Theta assembly and symmetrisation.
-Steps cycle over ten datasets (seeds 0..9), all resident in HBM.
+one pass of the whole path over a batch of ten datasets (seeds 0..9,
+resident in HBM) through the batched C ABI: Gram S = X'X/n, standardisation,
+coordinate descent with sigma updates, Theta assembly and symmetrisation, one
+launch per phase for all ten fits.  The plain path (one spmesl_gram +
+spmesl_fit per fit, serialised on one stream) is timed beside it.
 
 JSON line fields beyond the base contract:
   e2e          the same metric through spmesl_solve with HOST buffers (X copied
@@ -37,7 +39,7 @@ if ROOT not in sys.path:
 METRIC = "SPMESL solves/s + p99 latency, mixed-prec batched vs plain GPU @ dTheta<=1e-4"
 WORKLOAD = "er_p2000_n200_fp32"
 N_DATASETS = 10
-KERNELS_PER_SOLVE = 5        # gram, prep_diag, prep_matrix, cd_column, theta
+KERNELS_PER_SOLVE = 5        # per batched step: gram, prep_diag, prep_matrix, cd, theta
 
 
 def _env_rank():
@@ -159,6 +161,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _sha_of(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+CD_SOURCES = ["paper_2203_15031_gb300/csrc/cd_device.cuh", "paper_2203_15031_gb300/csrc/batch.cu"]
+PROFILE = "profiles/batch_cd_kernel_er_p2000_n200_x10.md"
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the batched CD kernel from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    try:
+        text = open(os.path.join(ROOT, PROFILE)).read()
+    except OSError:
+        return None
+    vals = dict(ln.split(":", 1) for ln in text.splitlines() if ":" in ln and ln[:1].isalpha())
+    try:
+        if vals.get("kernel_source_sha256", "").strip() != _sha_of(CD_SOURCES):
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -174,56 +205,38 @@ def run_ours(args):
     sp.lib()
 
     w, probs = make_inputs(N_DATASETS)
-    p, n = w["p"], w["n"]
-    lam = probs[0].lambda0
-    Xd = [torch.from_numpy(pr.X).to(dev) for pr in probs]
-    S = torch.empty((p, p), dtype=torch.float32, device=dev)
-    Theta = torch.empty((p, p), dtype=torch.float64, device=dev)
-    sigma = torch.empty(p, dtype=torch.float64, device=dev)
-    gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
-    fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
-    gkeep, gws = sp._workspace(gnb, dev)
-    fkeep, fws = sp._workspace(fnb, dev)
-    opts = sp.spmesl_default_opts()
-    opts.precision = sp.FP32
-    opts.record_phase_times = 1
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    p, n, tol, maxit = w["p"], w["n"], w["tol"], w["maxit"]
+    inputs = [(torch.from_numpy(pr.X).to(dev), pr.lambda0) for pr in probs]
     stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
-    def step(i):
-        X = Xd[i % N_DATASETS]
-        rc = sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S, p, gws, gnb, stream)
-        if rc != 0:
-            raise sp.SpmeslError(rc, "spmesl_gram")
-        rc = sp.spmesl_fit(S, n, p, lam, w["tol"], w["maxit"], opts, Theta, sigma, None, fws,
-                           fnb, stream)
-        if rc != 0:
-            raise sp.SpmeslError(rc, "spmesl_fit")
-
-    st = sp.Stats()
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    sp._check(sp.spmesl_fit_result(fws, p, sp.FP32, st, stream), "warmup", ok=(0,))
+    # ---- batched path (headline): one batch = the ten datasets
+    bt = sp.Batch(inputs, kind="X", precision="fp32", tol=tol, maxit=maxit,
+                  record_phase_times=True)
+    bt.run()
+    bt.result()
+    best_w = bt.tune()
+    for _ in range(args.warmup):
+        bt.run()
+    statuses, _ = bt.result()
+    if any(s != sp.SPMESL_OK for s in statuses):
+        raise RuntimeError(f"warm-up fits did not converge: {statuses}")
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    cd_ms, moves, sweeps = [], [], []
+    cd_ms, moves = [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         for i in range(args.steps):
-            flush.zero_()                     # evict X / S from L2 between solves
+            flush.zero_()                   # evict the inputs from L2 between steps
             ev[i][0].record(stream)
-            step(i)
+            bt.run(stream)
             ev[i][1].record(stream)
-            # phase times and counters of this solve (read after the event pair)
-            stream.synchronize()
-            sp.spmesl_fit_result(fws, p, sp.FP32, st, stream)
-            cd_ms.append(st.ms_cd)
-            moves.append(st.moves)
-            sweeps.append(st.inner_sweeps)
+            statuses, st = bt.result(stream)
+            cd_ms.append(st["ms_cd"])
+            moves.append(st["moves"])
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -233,69 +246,116 @@ def run_ours(args):
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value = world * N_DATASETS * args.steps / (total_ms / 1e3)
 
-    # end to end through the public API with host buffers (pinned)
-    Xh = [torch.from_numpy(pr.X).pin_memory() for pr in probs]
-    Th = torch.empty((p, p), dtype=torch.float64).pin_memory()
-    sh = torch.empty(p, dtype=torch.float64).pin_memory()
-    snb = sp.spmesl_solve_workspace_bytes(n, p, sp.FP32)
-    skeep, sws = sp._workspace(snb, dev)
-    sopts = sp.spmesl_default_opts()
-    sopts.precision = sp.FP32
+    # ---- plain path: one fit per launch sequence, serialised on one stream
+    S = torch.empty((p, p), dtype=torch.float32, device=dev)
+    Theta = torch.empty((p, p), dtype=torch.float64, device=dev)
+    sigma = torch.empty(p, dtype=torch.float64, device=dev)
+    gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
+    fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
+    gkeep, gws = sp._workspace(gnb, dev)
+    fkeep, fws = sp._workspace(fnb, dev)
+    opts = sp.spmesl_default_opts()
+    opts.precision = sp.FP32
+
+    def plain_fit(i):
+        X, lam = inputs[i % N_DATASETS]
+        sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S, p, gws, gnb, stream), "spmesl_gram")
+        sp._check(sp.spmesl_fit(S, n, p, lam, tol, maxit, opts, Theta, sigma, None, fws, fnb,
+                                stream), "spmesl_fit")
+
     for i in range(args.warmup):
-        sp._check(sp.spmesl_solve(Xh[i % N_DATASETS], n, p, lam, w["tol"], w["maxit"], sopts, Th,
-                                  sh, None, sws, snb, stream), "spmesl_solve")
+        plain_fit(i)
+    torch.cuda.synchronize()
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps * N_DATASETS)]
+    for s in range(args.steps):
+        flush.zero_()
+        for d in range(N_DATASETS):
+            e0, e1 = pev[s * N_DATASETS + d]
+            e0.record(stream)
+            plain_fit(d)
+            e1.record(stream)
+    torch.cuda.synchronize()
+    plain_per = [a.elapsed_time(b) for a, b in pev]
+    plain_value = len(plain_per) / (sum(plain_per) / 1e3)
+
+    # ---- end to end through the public API with host buffers (pinned)
+    Xh = [torch.from_numpy(pr.X).pin_memory() for pr in probs]
+    Th = [torch.empty((p, p), dtype=torch.float64).pin_memory() for _ in range(N_DATASETS)]
+    sh = [torch.empty(p, dtype=torch.float64).pin_memory() for _ in range(N_DATASETS)]
+
+    def e2e_step():
+        for d in range(N_DATASETS):
+            bt.inputs[d].copy_(Xh[d], non_blocking=True)
+        bt.run(stream)
+        for d in range(N_DATASETS):
+            Th[d].copy_(bt.Theta[d], non_blocking=True)
+            sh[d].copy_(bt.sigma[d], non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(args.warmup):
+        e2e_step()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        sp._check(sp.spmesl_solve(Xh[i % N_DATASETS], n, p, lam, w["tol"], w["maxit"], sopts, Th,
-                                  sh, None, sws, snb, stream), "spmesl_solve")
+    for _ in range(args.steps):
+        e2e_step()
     e2e_s = time.perf_counter() - t0
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
         dist.barrier()
-    e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
-           "h2d_bytes_per_step": n * p * 4, "d2h_bytes_per_step": p * p * 8 + p * 8}
+    e2e = {"value": world * N_DATASETS * args.steps / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": N_DATASETS * n * p * 4,
+           "d2h_bytes_per_step": N_DATASETS * (p * p * 8 + p * 8)}
 
     if rank == 0:
         hbm, which = _peaks()
-        # algorithmic bytes of one CD launch: every column loads S_.j once into
-        # shared memory and writes b_j once; every coordinate move reads one
-        # S row (the column slice of the rank-1 update).
+        # algorithmic bytes of one batched CD launch: every column loads S_.j
+        # into shared memory and writes b_j back (2 p rows of ldp floats per
+        # fit), and every coordinate move reads one S row (the column slice
+        # of the rank-1 update).
         ldp = (p + 31) // 32 * 32
         mv = statistics.mean(moves)
-        bytes_cd = 4.0 * ldp * (2 * p + mv)
+        bytes_cd = 4.0 * ldp * (2 * p * N_DATASETS + mv)
         cd_mean_ms = statistics.mean(cd_ms)
         achieved = bytes_cd / (cd_mean_ms / 1e3) / 1e9
+        traffic = measured_traffic()
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": "cd_column_kernel<float>",
-                "peak_kind": which, "algorithmic_bytes_per_launch": bytes_cd,
-                "mean_launch_ms": cd_mean_ms, "moves_per_launch": mv,
-                "sweeps_per_launch": statistics.mean(sweeps)}
-        per_sorted = sorted(per)
-        lat = {"p50_ms": statistics.median(per),
-               "p99_ms": per_sorted[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)],
-               "unit": "ms per solve (device)"}
+                "frac": achieved / hbm, "traffic": traffic,
+                "kernel": "batch_cd_kernel<float,1>", "peak_kind": which,
+                "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cd_mean_ms,
+                "moves_per_launch": mv, "warps_per_block": best_w}
+        srt = sorted(per)
+        psrt = sorted(plain_per)
+        q99 = lambda v: v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)]
+        lat = {"batched_p50_ms": statistics.median(per), "batched_p99_ms": q99(srt),
+               "plain_p50_ms": statistics.median(plain_per), "plain_p99_ms": q99(psrt),
+               "unit": "ms from launch to completion of a solve (device)"}
         cb = cpu_baseline(w, probs[0]) if world == 1 and not args.no_cpu_baseline else None
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "p": p, "n": n, "network": "erdos_renyi",
-                           "datasets": N_DATASETS, "lambda0": "sqrt(2 log p / n)",
-                           "tol": w["tol"], "maxit": w["maxit"], "gram": "fp32",
-                           "inner_rule": "column", "l2": "flushed between steps (256 MB write)",
+                           "fits_per_step": N_DATASETS, "seeds": "0-9",
+                           "lambda0": "sqrt(2 log p / n)", "tol": tol, "maxit": maxit,
+                           "gram": "fp32", "cd": "fp32", "sigma_theta": "fp64",
+                           "inner_rule": "column", "path": "batched (one launch per phase)",
+                           "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}"},
+                "plain": {"value": plain_value, "unit": "solves/s",
+                          "path": "one spmesl_gram + spmesl_fit per fit, serialised"},
                 "latency": lat, "e2e": e2e, "roofline": roof, "cpu_baseline": cb,
                 "gpu_launches": KERNELS_PER_SOLVE * args.steps,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    del gkeep, fkeep, skeep
+    bt.close()
+    del gkeep, fkeep
     if world > 1:
         dist.destroy_process_group()
 

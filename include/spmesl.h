@@ -74,6 +74,17 @@ typedef enum {
     SPMESL_INNER_COLUMN = 1     /* per column ||b_next - b_cur||_inf (Algorithms 1-2) */
 } spmesl_inner_rule;
 
+/* How the per-column rule keeps g_j = S_.j - S b_j during a sweep.  Both give
+ * the iterates of Algorithm 1; they differ in memory use only. */
+typedef enum {
+    SPMESL_GRADIENT_AUTO = 0,   /* lazy, with the eager solver for columns whose support
+                                   outgrows the lazy solver's list (512 entries) */
+    SPMESL_GRADIENT_EAGER = 1,  /* g_j and b_j stored in shared memory, rank-1 update of the
+                                   whole g_j after every coordinate move */
+    SPMESL_GRADIENT_LAZY = 2    /* only the support of b_j stored; each 128-coordinate slice of
+                                   g_j formed from S rows when the sweep reaches it (same as AUTO) */
+} spmesl_gradient;
+
 typedef struct {
     int32_t precision;          /* spmesl_precision */
     int32_t standardize;        /* 1 (default): fit on S^C = C S C, C = diag(S_jj^-1/2), and
@@ -87,7 +98,8 @@ typedef struct {
                                    spmesl_fit_result then fills ms_cd and ms_theta */
     int32_t use_graph;          /* spmesl_batch_run: capture the batch's launches once into a
                                    CUDA graph and replay it on later runs */
-    int32_t reserved[8];
+    int32_t gradient;           /* spmesl_gradient: how a column keeps its gradient (column rule) */
+    int32_t reserved[7];
 } spmesl_opts;
 
 typedef struct {

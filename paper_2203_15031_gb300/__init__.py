@@ -37,6 +37,7 @@ SPMESL_ETIMEOUT, SPMESL_ECUDA, SPMESL_EBUSY, SPMESL_ENOTFOUND = -5, -6, -7, -8
 FP64, FP32, MIXED = 0, 1, 2
 LAMBDA_GIVEN, LAMBDA_UNIV, LAMBDA_UNIV_PM1, LAMBDA_UB, LAMBDA_PB = 0, 1, 2, 3, 4
 INNER_JOINT, INNER_COLUMN = 0, 1
+GRADIENT_AUTO, GRADIENT_EAGER, GRADIENT_LAZY = 0, 1, 2
 _PREC = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
 
 
@@ -45,7 +46,7 @@ class Opts(ctypes.Structure):
                 ("center", ctypes.c_int32), ("lambda_rule", ctypes.c_int32),
                 ("inner_rule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("record_phase_times", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("gradient", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class Problem(ctypes.Structure):
@@ -264,7 +265,7 @@ def gram(X, precision="fp32", center=False, stream=None):
 
 def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=True,
         inner_rule=INNER_COLUMN, lambda_rule=LAMBDA_GIVEN, warps_per_block=0,
-        return_B=False, stream=None):
+        gradient=GRADIENT_AUTO, return_B=False, stream=None):
     """One fit on a CUDA covariance tensor.  Synchronises and returns
     (Theta, sigma, stats_dict[, B])."""
     import torch
@@ -277,6 +278,7 @@ def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=Tru
     opts.inner_rule = int(inner_rule)
     opts.lambda_rule = int(lambda_rule)
     opts.warps_per_block = int(warps_per_block)
+    opts.gradient = int(gradient)
     Theta = torch.empty((p, p), dtype=torch.float64, device=S.device)
     sigma = torch.empty(p, dtype=torch.float64, device=S.device)
     nb = spmesl_fit_workspace_bytes(p, prec)
@@ -337,7 +339,8 @@ class Batch:
     outputs ``Theta[i]`` / ``sigma[i]`` are allocated here."""
 
     def __init__(self, inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000,
-                 use_graph=False, warps_per_block=0, center=False, device=None):
+                 use_graph=False, warps_per_block=0, center=False, record_phase_times=False,
+                 gradient=GRADIENT_AUTO, device=None):
         import torch
         _require_cuda()
         prec = _prec(precision)
@@ -364,6 +367,8 @@ class Batch:
         opts.use_graph = int(bool(use_graph))
         opts.warps_per_block = int(warps_per_block)
         opts.center = int(bool(center))
+        opts.record_phase_times = int(bool(record_phase_times))
+        opts.gradient = int(gradient)
         rc, self.handle = spmesl_batch_create(arr, self.count, tol, maxit, opts)
         _check(rc, "spmesl_batch_create")
         self.ws_bytes = spmesl_batch_workspace_bytes(self.handle)

@@ -174,6 +174,7 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
         return SPMESL_EINVAL;
     if (o.inner_rule != SPMESL_INNER_JOINT && o.inner_rule != SPMESL_INNER_COLUMN)
         return SPMESL_EINVAL;
+    if (o.gradient < SPMESL_GRADIENT_AUTO || o.gradient > SPMESL_GRADIENT_LAZY) return SPMESL_EINVAL;
     if (p > max_p_for(o.precision)) return SPMESL_EINVAL;
     if (reinterpret_cast<uintptr_t>(workspace) & 255u) return SPMESL_EINVAL;
     if (ws_bytes < fit_layout(p, o.precision).total) return SPMESL_EINVAL;
@@ -200,6 +201,7 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
     f.standardize = o.standardize ? 1 : 0;
     f.inner_rule = o.inner_rule;
     f.warps_per_block = o.warps_per_block;
+    f.gradient = o.gradient;
     f.Theta = Theta;
     f.sigma_out = sigma;
     f.ws = static_cast<unsigned char*>(workspace);

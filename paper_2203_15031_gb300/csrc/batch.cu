@@ -42,8 +42,10 @@ struct BatchFit {
 };
 
 struct BatchHeader {
-    int next_col;
-    int pad[63];
+    int next_col;         // column queue of the first coordinate-descent launch
+    int ovf_count;        // columns handed from the lazy to the eager kernel
+    int ovf_next;         // eager kernel's position in that queue
+    int pad[61];
 };
 
 // Largest f with prefix[f] <= idx (prefix ascending, prefix[0] = 0).
@@ -116,16 +118,77 @@ __global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits) {
     if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
 }
 
+template <typename T>
+__device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, int maxit) {
+    CDArgs<T> a;
+    a.SC = static_cast<const T*>(f.SC);
+    a.BT = static_cast<T*>(f.BT);
+    a.GT = nullptr;
+    a.diag = static_cast<const T*>(f.diag);
+    a.sigma = f.sigma;
+    a.col_status = f.col_status;
+    a.active = a.active_next = a.flag = nullptr;
+    a.ctrl = f.ctrl;
+    a.p = f.p;
+    a.ldp = f.ldp;
+    a.maxit = maxit;
+    a.lambda0 = f.lambda0;
+    a.tol = tol;
+    a.ovf_list = nullptr;
+    a.ovf_count = nullptr;
+    return a;
+}
+
+// Eager gradient over all columns of all fits, or (from_queue) over the
+// global columns the lazy kernel handed over.
 template <typename T, bool STD>
 __global__ void __launch_bounds__(512) batch_cd_kernel(const BatchFit* __restrict__ fits,
                                                        const int* __restrict__ col_prefix,
                                                        int count, int total_cols, int max_ldp,
                                                        double tol, int maxit,
-                                                       BatchHeader* hdr) {
+                                                       BatchHeader* hdr, const int* ovf_list,
+                                                       int from_queue) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     T* g = reinterpret_cast<T*>(smem_raw + (size_t)warp * warp_smem_bytes<T>(max_ldp));
+    const int nq = from_queue ? *reinterpret_cast<volatile int*>(&hdr->ovf_count) : 0;
+    for (;;) {
+        int gc = 0;
+        if (from_queue) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&hdr->ovf_next, 1);
+            t = __shfl_sync(FULL_MASK, t, 0);
+            if (t >= nq) break;
+            gc = ovf_list[t];
+        } else {
+            if (lane == 0) gc = atomicAdd(&hdr->next_col, 1);
+            gc = __shfl_sync(FULL_MASK, gc, 0);
+            if (gc >= total_cols) break;
+        }
+        const int fi = find_fit(col_prefix, count, gc);
+        const BatchFit& f = fits[fi];
+        if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) continue;
+        const CDArgs<T> a = column_args<T>(f, tol, maxit);
+        T* b = g + f.ldp;
+        int* list = reinterpret_cast<int*>(b + f.ldp);
+        ColCounters cnt;
+        solve_column<T, STD>(gc - f.col_start, g, b, list, a, cnt);
+        flush_counters(f.ctrl, cnt);
+    }
+}
+
+// Lazy gradient over all columns of all fits; overflowing columns are queued.
+template <typename T, bool STD>
+__global__ void __launch_bounds__(512) batch_cd_lazy_kernel(const BatchFit* __restrict__ fits,
+                                                            const int* __restrict__ col_prefix,
+                                                            int count, int total_cols, int max_ldp,
+                                                            double tol, int maxit,
+                                                            BatchHeader* hdr, int* ovf_list) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char* wsm = smem_raw + (size_t)warp * lazy_warp_smem_bytes<T>(max_ldp);
     for (;;) {
         int gc = 0;
         if (lane == 0) gc = atomicAdd(&hdr->next_col, 1);
@@ -134,24 +197,11 @@ __global__ void __launch_bounds__(512) batch_cd_kernel(const BatchFit* __restric
         const int fi = find_fit(col_prefix, count, gc);
         const BatchFit& f = fits[fi];
         if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) continue;
-        CDArgs<T> a;
-        a.SC = static_cast<const T*>(f.SC);
-        a.BT = static_cast<T*>(f.BT);
-        a.GT = nullptr;
-        a.diag = static_cast<const T*>(f.diag);
-        a.sigma = f.sigma;
-        a.col_status = f.col_status;
-        a.active = a.active_next = a.flag = nullptr;
-        a.ctrl = f.ctrl;
-        a.p = f.p;
-        a.ldp = f.ldp;
-        a.maxit = maxit;
-        a.lambda0 = f.lambda0;
-        a.tol = tol;
-        T* b = g + f.ldp;
-        int* list = reinterpret_cast<int*>(b + f.ldp);
+        const CDArgs<T> a = column_args<T>(f, tol, maxit);
         ColCounters cnt;
-        solve_column<T, STD>(gc - f.col_start, g, b, list, a, cnt);
+        if (!solve_column_lazy<T, STD>(gc - f.col_start, wsm, a, cnt) && lane == 0)
+            ovf_list[atomicAdd(&hdr->ovf_count, 1)] = gc;
+        __syncwarp();
         flush_counters(f.ctrl, cnt);
     }
 }
@@ -220,6 +270,8 @@ struct spmesl_batch {
     double tol = 1e-6;
     int maxit = 1000;
     int warps_per_block = 0;       // 0 = automatic
+    int gradient = SPMESL_GRADIENT_AUTO;
+    size_t off_ovf = 0;            // queue of columns for the eager launch (total_cols ints)
     std::vector<FitPlan> plan;     // ordered by decreasing p
     size_t off_hdr = 0, off_desc = 0, off_colp = 0, off_gramp = 0, off_thetap = 0, off_ctrls = 0;
     size_t ws_bytes = 0;
@@ -233,6 +285,10 @@ struct spmesl_batch {
     const void* graph_ws = nullptr;
     int graph_W = -1;
     cudaStream_t cap_stream = nullptr;
+    // record_phase_times (runs without a graph): events around the CD launch
+    int record_phase_times = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool ev_recorded = false;
 };
 
 namespace {
@@ -263,24 +319,49 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     const int mx = std::max(1, std::min(64, (int)(((size_t)b->max_p * b->max_ldp + 8191) / 8192)));
     batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits);
 
-    const size_t per_warp = warp_smem_bytes<T>(b->max_ldp);
     const size_t budget = (size_t)max_smem_block() - 1024;
+    const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
+    int* ovf = reinterpret_cast<int*>(ws + b->off_ovf);
+    const bool timed = b->record_phase_times && b->ev[0];
+    if (timed) cudaEventRecord(b->ev[0], st);
+    if (lazy) {
+        // W (tuned) shapes the lazy launch, which does almost all the work
+        const size_t lper = lazy_warp_smem_bytes<T>(b->max_ldp);
+        const int LW = std::max(1, std::min({W, 16, (int)(budget / lper)}));
+        const size_t lsm = lper * LW;
+        auto lk = b->standardize ? batch_cd_lazy_kernel<T, true> : batch_cd_lazy_kernel<T, false>;
+        if ((e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lsm)) != cudaSuccess)
+            return e;
+        int lper_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper_sm, lk, 32 * LW, lsm)) !=
+            cudaSuccess)
+            return e;
+        lper_sm = std::max(lper_sm, 1);
+        const int lgrid = std::min((b->total_cols + LW - 1) / LW, num_sms() * lper_sm);
+        lk<<<lgrid, 32 * LW, lsm, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
+                                        b->maxit, hdr, ovf);
+    }
+    // eager launch: every column, or only the queue the lazy launch left
+    const size_t per_warp = warp_smem_bytes<T>(b->max_ldp);
     const int wmax = (int)std::min<size_t>(16, budget / per_warp);
     if (wmax < 1) return cudaErrorInvalidValue;
-    W = std::max(1, std::min(W, wmax));
-    const size_t smem = per_warp * W;
+    int EW = lazy ? (int)std::max<size_t>(1, (budget / 2) / per_warp) : W;
+    EW = std::max(1, std::min(EW, wmax));
+    const size_t smem = per_warp * EW;
     auto kern = b->standardize ? batch_cd_kernel<T, true> : batch_cd_kernel<T, false>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * W, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * EW, smem)) !=
         cudaSuccess)
         return e;
     per_sm = std::max(per_sm, 1);
-    const int grid = std::min((b->total_cols + W - 1) / W, num_sms() * per_sm);
-    kern<<<grid, 32 * W, smem, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
-                                     b->maxit, hdr);
+    const int grid = std::min((b->total_cols + EW - 1) / EW, num_sms() * per_sm);
+    kern<<<grid, 32 * EW, smem, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
+                                      b->maxit, hdr, ovf, lazy ? 1 : 0);
+    if (timed) cudaEventRecord(b->ev[1], st);
     batch_theta_kernel<T><<<b->total_theta, dim3(32, 8), 0, st>>>(fits, thetap, count);
     return cudaGetLastError();
 }
@@ -288,6 +369,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
 // Default warps per block: fill every SM with enough warps for the columns,
 // keeping shared memory near half of the SM (see the single-fit launcher).
 int auto_warps(const spmesl_batch* b) {
+    if (b->gradient != SPMESL_GRADIENT_EAGER) return 8;    // lazy launch: 8 warps per block
     const size_t per_warp = b->precision == SPMESL_FP64 ? warp_smem_bytes<double>(b->max_ldp)
                                                         : warp_smem_bytes<float>(b->max_ldp);
     const size_t budget = (size_t)max_smem_block() - 1024;
@@ -374,7 +456,9 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->standardize = o.standardize ? 1 : 0;
     b->center = o.center ? 1 : 0;
     b->use_graph = o.use_graph ? 1 : 0;
+    b->record_phase_times = o.record_phase_times ? 1 : 0;
     b->warps_per_block = o.warps_per_block;
+    b->gradient = o.gradient;
     b->tol = tol;
     b->maxit = maxit;
     std::vector<int> order(count);
@@ -434,6 +518,8 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->total_cols = cols;
     b->total_gram = gram;
     b->total_theta = theta;
+    b->off_ovf = off;
+    off += align_up(sizeof(int) * (size_t)cols, 256);
     b->ws_bytes = off;
     if (cudaMallocHost(&b->pinned, b->table_bytes) != cudaSuccess) {
         delete b;
@@ -461,9 +547,15 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
                                            : enqueue_batch<float>(b, ws, s2, W);
     };
     if (!b->use_graph) {
+        if (b->record_phase_times && !b->ev[0]) {
+            if (cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess)
+                return SPMESL_ECUDA;
+        }
         cudaError_t e = enqueue(st);
+        b->ev_recorded = b->record_phase_times && e == cudaSuccess;
         return e == cudaSuccess ? SPMESL_OK : SPMESL_ECUDA;
     }
+    b->ev_recorded = false;
     if (!b->graph || b->graph_ws != workspace || b->graph_W != W) {
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
@@ -520,6 +612,10 @@ spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, 
         agg.max_col_outer = std::max(agg.max_col_outer, c.outer_max);
     }
     agg.status = worst;
+    if (b->ev_recorded) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) agg.ms_cd = ms;
+    }
     if (stats) *stats = agg;
     return worst;
 }
@@ -569,6 +665,8 @@ void spmesl_batch_destroy(spmesl_batch* b) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->ev[0]) cudaEventDestroy(b->ev[0]);
+    if (b->ev[1]) cudaEventDestroy(b->ev[1]);
     if (b->pinned) cudaFreeHost(b->pinned);
     delete b;
 }

@@ -29,8 +29,10 @@ namespace spmesl {
 // Per-column rule (Algorithms 1-2): every warp takes the next unsolved column
 // and runs the whole scaled lasso for it; no grid-wide synchronisation.
 // ---------------------------------------------------------------------------
+// Eager gradient (g_j and b_j in shared memory).  With from_queue the warps
+// take the columns the lazy solver handed over instead of 0..p-1.
 template <typename T, bool STD>
-__global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a) {
+__global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a, int from_queue) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -39,13 +41,45 @@ __global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a) {
     int* list = reinterpret_cast<int*>(b + a.ldp);
     FitCtrl* ctrl = a.ctrl;
     if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
+    const int nq = from_queue ? *reinterpret_cast<volatile int*>(a.ovf_count) : 0;
+    ColCounters cnt;
+    for (;;) {
+        int j = 0;
+        if (from_queue) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&ctrl->ovf_next, 1);
+            t = __shfl_sync(FULL_MASK, t, 0);
+            if (t >= nq) break;
+            j = a.ovf_list[t];
+        } else {
+            if (lane == 0) j = atomicAdd(&ctrl->next_col, 1);
+            j = __shfl_sync(FULL_MASK, j, 0);
+            if (j >= a.p) break;
+        }
+        solve_column<T, STD>(j, g, b, list, a, cnt);
+    }
+    flush_counters(ctrl, cnt);
+}
+
+// Lazy gradient (sorted support in shared memory); columns whose support
+// outgrows the list go to the queue for cd_column_kernel.
+template <typename T, bool STD>
+__global__ void __launch_bounds__(512) cd_column_lazy_kernel(CDArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char* wsm = smem_raw + (size_t)warp * lazy_warp_smem_bytes<T>(a.ldp);
+    FitCtrl* ctrl = a.ctrl;
+    if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
     ColCounters cnt;
     for (;;) {
         int j = 0;
         if (lane == 0) j = atomicAdd(&ctrl->next_col, 1);
         j = __shfl_sync(FULL_MASK, j, 0);
         if (j >= a.p) break;
-        solve_column<T, STD>(j, g, b, list, a, cnt);
+        if (!solve_column_lazy<T, STD>(j, wsm, a, cnt) && lane == 0)
+            a.ovf_list[atomicAdd(a.ovf_count, 1)] = j;
+        __syncwarp();
     }
     flush_counters(ctrl, cnt);
 }
@@ -164,7 +198,11 @@ __global__ void __launch_bounds__(512) cd_joint_kernel(CDArgs<T> a) {
                     __syncwarp();
                 }
                 const T lam = (T)(a.sigma[j] * a.lambda0);
-                wmax = fmax(wmax, sweep_column<T, STD>(j, g, b, a, lam, moves));
+                // no summaries carried between joint sweeps: every chunk is scanned
+                ColScan cs{reinterpret_cast<ChunkInfo*>(list + SUPP_CAP), 0.f, 0u};
+                reset_chunks(cs, a.ldp);
+                __syncwarp();
+                wmax = fmax(wmax, sweep_column<T, STD>(j, g, b, a, lam, moves, cs));
                 if (!resident) {
                     warp_copy<T>(a.GT + (size_t)j * a.ldp, g, a.ldp);
                     warp_copy<T>(a.BT + (size_t)j * a.ldp, b, a.ldp);
@@ -324,12 +362,16 @@ static cudaError_t device_limits() {
 static size_t smem_budget() { return (size_t)g_max_smem_block - 1024; }
 
 int max_p_for(int precision) {
-    // one warp needs g and b: 2 * ldp * s bytes; the opt-in block limit on
-    // GB300 is 227 KB.
-    const size_t budget = 232448 - 1024 - SUPP_CAP * sizeof(int);
-    const size_t s = (size_t)elem_size(precision);
-    int p = (int)(budget / (2 * s));
-    return p / 32 * 32;
+    // one warp needs warp_smem_bytes(ldp) of shared memory; the opt-in block
+    // limit on GB300 is 227 KB.
+    const size_t budget = 232448 - 1024;
+    int p = 32;
+    if (precision == SPMESL_FP64) {
+        while (warp_smem_bytes<double>(p + 32) <= budget) p += 32;
+    } else {
+        while (warp_smem_bytes<float>(p + 32) <= budget) p += 32;
+    }
+    return p;
 }
 
 template <typename T, bool STD>
@@ -354,6 +396,8 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     a.maxit = f.maxit;
     a.lambda0 = f.lambda0;
     a.tol = f.tol;
+    a.ovf_list = a.flag;            // the column rule does not use the flag array
+    a.ovf_count = &ctrl->ovf_count;
     const bool joint = f.inner_rule == SPMESL_INNER_JOINT;
 
     if ((e = cudaMemsetAsync(ctrl, 0, sizeof(FitCtrl), st)) != cudaSuccess) return e;
@@ -390,6 +434,26 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
 
     if (f.phase_events) cudaEventRecord(f.phase_events[0], st);
     if (!joint) {
+        const bool lazy = f.gradient != SPMESL_GRADIENT_EAGER;
+        if (lazy) {
+            // lazy gradient: small shared-memory footprint, many columns per SM
+            auto lk = cd_column_lazy_kernel<T, STD>;
+            const size_t lper = lazy_warp_smem_bytes<T>(L.ldp);
+            int LW = f.warps_per_block > 0 ? f.warps_per_block : 8;
+            LW = std::max(1, std::min({LW, 16, (int)(smem_budget() / lper)}));
+            const size_t lsm = lper * LW;
+            if ((e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)lsm)) != cudaSuccess)
+                return e;
+            int lper_sm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper_sm, lk, 32 * LW, lsm)) !=
+                cudaSuccess)
+                return e;
+            lper_sm = std::max(lper_sm, 1);
+            const int lgrid = std::min((f.p + LW - 1) / LW, g_num_sms * lper_sm);
+            lk<<<lgrid, 32 * LW, lsm, st>>>(a);
+        }
+        // eager gradient: all columns, or only those the lazy solver handed over
         auto kern = cd_column_kernel<T, STD>;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem)) != cudaSuccess)
@@ -400,7 +464,7 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
             return e;
         per_sm = auto_shape ? 1 : std::max(per_sm, 1);
         const int grid = std::min((f.p + W - 1) / W, g_num_sms * per_sm);
-        kern<<<grid, threads, smem, st>>>(a);
+        kern<<<grid, threads, smem, st>>>(a, lazy ? 1 : 0);
     } else {
         auto kern = cd_joint_kernel<T, STD>;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -22,6 +22,8 @@ struct CDArgs {
     FitCtrl* ctrl;
     int p, ldp, maxit;
     double lambda0, tol;
+    int* ovf_list;       // columns handed from the lazy solver to the eager one
+    int* ovf_count;
 };
 
 template <typename T>
@@ -114,81 +116,157 @@ __device__ __forceinline__ void load4(const T* __restrict__ src, T (&v)[4]) {
 }
 
 // Each lane evaluates 4 consecutive coordinates, so one step of the warp
-// covers 128 coordinates; the first coordinate whose update changes b is
-// applied and the scan resumes right after it.
+// covers a 128-coordinate chunk; the first coordinate whose update changes b
+// is applied and the scan resumes right after it within the chunk.
 constexpr int SCAN_V = 4;
+constexpr int CHUNK = 32 * SCAN_V;
+
+// Per-chunk summary kept between sweeps for the skip test (standardised
+// working matrix only): after the chunk was last scanned, the largest |g_k|
+// over its coordinates with b_k = 0, how many of its b_k were nonzero, and
+// the running sum of |delta| and move count at that moment.
+struct ChunkInfo {
+    float maxabs;
+    float dsum_at;
+    unsigned moves_at;
+    int nsupp;
+};
+
+// Scan state of one column solve (warp-uniform).
+struct ColScan {
+    ChunkInfo* ci;
+    float dsum;          // sum of |delta| over all moves of this column so far
+    unsigned nmoves;     // number of those moves
+};
+
+// A chunk with no support can be skipped when no coordinate in it can reach
+// the threshold: each move delta_m at row m changes g_k by -S_km delta_m with
+// |S_km| <= 1 (standardised), so |g_k| <= maxabs + sum|delta| since the chunk
+// was scanned.  The margins cover FP32 rounding of the standardised S
+// (|S_km| <= 1 + 2^-22), of every g update (half an ulp of a value below
+// lambda) and of the running sum; after 4096 moves the chunk is always
+// rescanned.  A skipped coordinate therefore has |g_k| < lambda and b_k = 0,
+// so it would not have moved: the sweep is the same as a full scan.
+__device__ __forceinline__ bool chunk_skippable(const ChunkInfo& c, const ColScan& cs, float lam) {
+    const unsigned dm = cs.nmoves - c.moves_at;
+    if (c.nsupp != 0 || dm > 4096u) return false;
+    const float bound = c.maxabs + (cs.dsum - c.dsum_at) * (1.0f + 0x1p-10f) +
+                        cs.dsum * 0x1p-21f + (float)dm * lam * 0x1p-20f;
+    return bound < lam;
+}
 
 template <typename T, bool STD>
 __device__ T sweep_column(int j, T* __restrict__ g, T* __restrict__ b, const CDArgs<T>& a, T lam,
-                          unsigned long long& moves) {
+                          unsigned long long& moves, ColScan& cs) {
     const int lane = threadIdx.x & 31;
     const int p = a.p;
     const int ldp = a.ldp;
     T maxd = T(0);
-    int cursor = 0;
-    while (cursor < p) {
-        const int base = cursor & ~(SCAN_V - 1);
-        const int k0 = base + lane * SCAN_V;
-        T gv[SCAN_V], bv[SCAN_V], nbv[SCAN_V];
-        if (k0 < ldp) {                       // ldp is a multiple of 32: the whole quad is in range
-            load4<T>(g + k0, gv);
-            load4<T>(b + k0, bv);
-        } else {
-#pragma unroll
-            for (int t = 0; t < SCAN_V; ++t) gv[t] = bv[t] = T(0);
+    for (int cb = 0, ci = 0; cb < p; cb += CHUNK, ++ci) {
+        if constexpr (STD) {
+            if (chunk_skippable(cs.ci[ci], cs, (float)lam)) continue;
         }
-        unsigned mvmask = 0u;
+        const int k0 = cb + lane * SCAN_V;
+        int cursor = cb;
+        for (;;) {
+            T gv[SCAN_V], bv[SCAN_V], nbv[SCAN_V];
+            if (k0 < ldp) {                   // ldp is a multiple of 32: the whole quad is in range
+                load4<T>(g + k0, gv);
+                load4<T>(b + k0, bv);
+            } else {
 #pragma unroll
-        for (int t = 0; t < SCAN_V; ++t) {
-            const int k = k0 + t;
-            nbv[t] = bv[t];
-            if (k >= cursor && k < p && k != j) {
-                T nb;
-                if constexpr (STD) {
-                    nb = soft<T>(gv[t] + bv[t], lam);                  // S_kk = 1
-                } else {
-                    const T skk = a.diag[k];
-                    nb = soft<T>(gv[t] + skk * bv[t], lam) / skk;      // Soft(c, lambda)/S_kk
-                }
-                nbv[t] = nb;
-                if (nb != bv[t]) mvmask |= 1u << t;
+                for (int t = 0; t < SCAN_V; ++t) gv[t] = bv[t] = T(0);
             }
-        }
-        const unsigned bal = __ballot_sync(FULL_MASK, mvmask != 0u);
-        if (bal == 0u) {
-            cursor = base + 32 * SCAN_V;
-            continue;
-        }
-        const int f = __ffs(bal) - 1;
-        const int tf = __ffs(__shfl_sync(FULL_MASK, mvmask, f)) - 1;
-        T nb_sel = nbv[0], b_sel = bv[0];
+            unsigned mvmask = 0u;
 #pragma unroll
-        for (int t = 1; t < SCAN_V; ++t)
-            if (t == tf) { nb_sel = nbv[t]; b_sel = bv[t]; }
-        const T nbs = __shfl_sync(FULL_MASK, nb_sel, f);
-        const T delta = nbs - __shfl_sync(FULL_MASK, b_sel, f);
-        const int ks = base + f * SCAN_V + tf;
-        if (lane == 0) b[ks] = nbs;
-        maxd = fmax(maxd, fabs(delta));
-        ++moves;
-        axpy_row<T>(g, a.SC + (size_t)ks * ldp, delta, ldp);
-        __syncwarp();
-        cursor = ks + 1;
+            for (int t = 0; t < SCAN_V; ++t) {
+                const int k = k0 + t;
+                nbv[t] = bv[t];
+                if (k >= cursor && k < p && k != j) {
+                    T nb;
+                    if constexpr (STD) {
+                        nb = soft<T>(gv[t] + bv[t], lam);                  // S_kk = 1
+                    } else {
+                        const T skk = a.diag[k];
+                        nb = soft<T>(gv[t] + skk * bv[t], lam) / skk;      // Soft(c, lambda)/S_kk
+                    }
+                    nbv[t] = nb;
+                    if (nb != bv[t]) mvmask |= 1u << t;
+                }
+            }
+            const unsigned bal = __ballot_sync(FULL_MASK, mvmask != 0u);
+            if (bal == 0u) break;
+            const int f = __ffs(bal) - 1;
+            const int tf = __ffs(__shfl_sync(FULL_MASK, mvmask, f)) - 1;
+            T nb_sel = nbv[0], b_sel = bv[0];
+#pragma unroll
+            for (int t = 1; t < SCAN_V; ++t)
+                if (t == tf) { nb_sel = nbv[t]; b_sel = bv[t]; }
+            const T nbs = __shfl_sync(FULL_MASK, nb_sel, f);
+            const T delta = nbs - __shfl_sync(FULL_MASK, b_sel, f);
+            const int ks = cb + f * SCAN_V + tf;
+            if (lane == 0) b[ks] = nbs;
+            maxd = fmax(maxd, fabs(delta));
+            ++moves;
+            cs.dsum += fabsf((float)delta);
+            ++cs.nmoves;
+            axpy_row<T>(g, a.SC + (size_t)ks * ldp, delta, ldp);
+            __syncwarp();
+            cursor = ks + 1;
+            if (cursor >= cb + CHUNK) break;
+        }
+        if constexpr (STD) {
+            // summary of the chunk as it leaves the scan
+            float mx = 0.f;
+            int ns = 0;
+            if (k0 < ldp) {
+                T gv[SCAN_V], bv[SCAN_V];
+                load4<T>(g + k0, gv);
+                load4<T>(b + k0, bv);
+#pragma unroll
+                for (int t = 0; t < SCAN_V; ++t) {
+                    const int k = k0 + t;
+                    if (k < p && k != j) {
+                        if (bv[t] != T(0)) ++ns;
+                        else mx = fmaxf(mx, fabsf((float)gv[t]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+                ns += __shfl_xor_sync(FULL_MASK, ns, o);
+            }
+            if (lane == 0) cs.ci[ci] = ChunkInfo{mx, cs.dsum, cs.nmoves, ns};
+            __syncwarp();
+        }
     }
     return maxd;
 }
 
-// sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the support of b
-// (Eq. (14) written on S).  Same value in every lane.
+// Mark every chunk "must scan" (a chunk with nsupp != 0 is never skipped).
+__device__ __forceinline__ void reset_chunks(ColScan& cs, int ldp) {
+    const int nc = (ldp + CHUNK - 1) / CHUNK;
+    for (int c = threadIdx.x & 31; c < nc; c += 32) cs.ci[c] = ChunkInfo{0.f, 0.f, 0u, 1};
+    cs.dsum = 0.f;
+    cs.nmoves = 0u;
+}
+
 // Per-warp scratch for the support list used by the sigma update.
 constexpr int SUPP_CAP = 128;
 
-// Shared memory of one warp: g_j and b_j (ldp elements each) and the list.
+// Shared memory of one warp: g_j and b_j (ldp elements each), the support
+// list and the chunk summaries.
+__host__ __device__ constexpr int num_chunks(int ldp) { return (ldp + CHUNK - 1) / CHUNK; }
+
 template <typename T>
 __host__ __device__ constexpr size_t warp_smem_bytes(int ldp) {
-    return 2 * (size_t)ldp * sizeof(T) + SUPP_CAP * sizeof(int);
+    return 2 * (size_t)ldp * sizeof(T) + SUPP_CAP * sizeof(int) +
+           (size_t)num_chunks(ldp) * sizeof(ChunkInfo);
 }
 
+// sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the support of b
+// (Eq. (14) written on S).  Same value in every lane.
 template <typename T>
 __device__ double residual_quadratic_form(int j, const T* __restrict__ b, const CDArgs<T>& a,
                                           int* __restrict__ list) {
@@ -275,6 +353,8 @@ __device__ void solve_column(int j, T* __restrict__ g, T* __restrict__ b, int* _
     const int lane = threadIdx.x & 31;
     warp_copy<T>(g, a.SC + (size_t)j * a.ldp, a.ldp);   // g = S_.j  (b = 0)
     warp_zero<T>(b, a.ldp);
+    ColScan cs{reinterpret_cast<ChunkInfo*>(list + SUPP_CAP), 0.f, 0u};
+    reset_chunks(cs, a.ldp);
     __syncwarp();
 
     double sigma = 1.0;                                  // sigma^(0) = 1
@@ -286,7 +366,7 @@ __device__ void solve_column(int j, T* __restrict__ g, T* __restrict__ b, int* _
         const T lam = (T)(sigma * a.lambda0);
         bool inner_ok = false;
         for (int m = 0; m < a.maxit; ++m) {
-            const T md = sweep_column<T, STD>(j, g, b, a, lam, cnt.moves);
+            const T md = sweep_column<T, STD>(j, g, b, a, lam, cnt.moves, cs);
             ++cnt.sweeps;
             if ((double)md < a.tol) {
                 inner_ok = true;
@@ -318,6 +398,289 @@ __device__ void solve_column(int j, T* __restrict__ g, T* __restrict__ b, int* _
     cnt.n_nc += (status & COL_NOT_CONVERGED) != 0;
     cnt.n_deg += (status & COL_DEGENERATE) != 0;
     __syncwarp();
+}
+
+// ===========================================================================
+// Lazy-gradient column solver.
+//
+// Same iterates as solve_column (Algorithm 1, ascending cyclic order), but
+// the gradient g = S_.j - S b is never stored.  The warp keeps only the
+// support of b_j, sorted by coordinate, in shared memory.  Each 128-coordinate
+// chunk forms its slice of g from coalesced 16-byte reads of row j and of the
+// rows of the support (S symmetric), so the chunk's reads are independent and
+// cost one round trip.  When a coordinate moves, the rank-1 update
+// g -= S_.k delta is applied at once to the rest of the chunk and reaches
+// every later chunk when that chunk forms its slice from the updated support.
+// This is the covariance form of c = S_kj - sum_{l != k} S_kl b_l.  With about
+// 5 KB of shared memory per column instead of two p-vectors, many more columns
+// stay resident per SM.
+// If the support outgrows the list, the column is handed to the eager solver
+// (solve_column) through a queue and solved again from the start.
+// ===========================================================================
+constexpr int LAZY_CAP = 512;
+
+template <typename T>
+struct Support {
+    int* idx;      // sorted coordinates with b != 0
+    T* val;        // their b values
+    int n;         // warp-uniform count
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t lazy_warp_smem_bytes(int ldp) {
+    return (size_t)LAZY_CAP * (sizeof(int) + sizeof(T)) + (size_t)num_chunks(ldp) * sizeof(ChunkInfo);
+}
+
+// Set b_k = v in the sorted support (insert, update or remove).  pos is the
+// first index with idx[pos] >= k.  Returns false if an insert would overflow.
+template <typename T>
+__device__ bool support_set(Support<T>& s, int pos, int k, T v) {
+    const int lane = threadIdx.x & 31;
+    const bool exists = pos < s.n && s.idx[pos] == k;
+    if (exists && v != T(0)) {
+        if (lane == 0) s.val[pos] = v;
+        __syncwarp();
+        return true;
+    }
+    if (!exists && v == T(0)) return true;
+    if (!exists && s.n >= LAZY_CAP) return false;
+    const int shift = exists ? -1 : 1;
+    const int from = exists ? pos + 1 : pos;        // entries [from, n) move by `shift`
+    const int cnt = s.n - from;
+    // move in register-sized rounds; the direction keeps every read ahead of its write
+    for (int base = 0; base < cnt; base += 32) {
+        const int t = shift > 0 ? cnt - 1 - (base + lane) : base + lane;
+        int ix = 0;
+        T vv = T(0);
+        const bool act = (base + lane) < cnt;
+        if (act) {
+            ix = s.idx[from + t];
+            vv = s.val[from + t];
+        }
+        __syncwarp();
+        if (act) {
+            s.idx[from + t + shift] = ix;
+            s.val[from + t + shift] = vv;
+        }
+        __syncwarp();
+    }
+    if (!exists && lane == 0) {
+        s.idx[pos] = k;
+        s.val[pos] = v;
+    }
+    s.n += shift;
+    __syncwarp();
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void load4g(const T* __restrict__ src, T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 q0 = __ldg(reinterpret_cast<const double2*>(src));
+        const double2 q1 = __ldg(reinterpret_cast<const double2*>(src + 2));
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+}
+
+// One sweep; returns max |delta b|.  Sets `overflow` and stops early if the
+// support list is full.
+template <typename T, bool STD>
+__device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
+                               unsigned long long& moves, ColScan& cs, bool& overflow) {
+    const int lane = threadIdx.x & 31;
+    const int p = a.p;
+    const int ldp = a.ldp;
+    const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
+    T maxd = T(0);
+    int e0 = 0;                                   // first support entry with idx >= cb
+    for (int cb = 0, ci = 0; cb < p; cb += CHUNK, ++ci) {
+        while (e0 < s.n && s.idx[e0] < cb) ++e0;
+        int e1 = e0;
+        while (e1 < s.n && s.idx[e1] < cb + CHUNK) ++e1;
+        if constexpr (STD) {
+            if (e1 == e0 && chunk_skippable(cs.ci[ci], cs, (float)lam)) continue;
+        }
+        const int k0 = cb + lane * SCAN_V;
+        const bool in = k0 < ldp;                 // the whole quad is inside the padded row
+        // slice of g: S_jk - sum_{l in support} S_lk b_l
+        T acc[SCAN_V] = {T(0), T(0), T(0), T(0)};
+        if (in) load4g<T>(Sj + k0, acc);
+#pragma unroll 4
+        for (int e = 0; e < s.n; ++e) {
+            const int l = s.idx[e];
+            const T v = s.val[e];
+            if (in) {
+                T r[SCAN_V];
+                load4g<T>(a.SC + (size_t)l * ldp + k0, r);
+#pragma unroll
+                for (int t = 0; t < SCAN_V; ++t) acc[t] = fma(-v, r[t], acc[t]);
+            }
+        }
+        // current b of this lane's coordinates (support entries of the chunk)
+        T bv[SCAN_V] = {T(0), T(0), T(0), T(0)};
+        for (int e = e0; e < e1; ++e) {
+            const int t = s.idx[e] - k0;
+            if (t >= 0 && t < SCAN_V) {
+#pragma unroll
+                for (int u = 0; u < SCAN_V; ++u)
+                    if (u == t) bv[u] = s.val[e];
+            }
+        }
+        int cursor = cb;
+        for (;;) {
+            T nbv[SCAN_V];
+            unsigned mvmask = 0u;
+#pragma unroll
+            for (int t = 0; t < SCAN_V; ++t) {
+                const int k = k0 + t;
+                nbv[t] = bv[t];
+                if (k >= cursor && k < p && k != j) {
+                    T nb;
+                    if constexpr (STD) {
+                        nb = soft<T>(acc[t] + bv[t], lam);                 // S_kk = 1
+                    } else {
+                        const T skk = a.diag[k];
+                        nb = soft<T>(acc[t] + skk * bv[t], lam) / skk;     // Soft(c, lambda)/S_kk
+                    }
+                    nbv[t] = nb;
+                    if (nb != bv[t]) mvmask |= 1u << t;
+                }
+            }
+            const unsigned bal = __ballot_sync(FULL_MASK, mvmask != 0u);
+            if (bal == 0u) break;
+            const int f = __ffs(bal) - 1;
+            const int tf = __ffs(__shfl_sync(FULL_MASK, mvmask, f)) - 1;
+            T nb_sel = nbv[0], b_sel = bv[0];
+#pragma unroll
+            for (int t = 1; t < SCAN_V; ++t)
+                if (t == tf) { nb_sel = nbv[t]; b_sel = bv[t]; }
+            const T nbs = __shfl_sync(FULL_MASK, nb_sel, f);
+            const T delta = nbs - __shfl_sync(FULL_MASK, b_sel, f);
+            const int ks = cb + f * SCAN_V + tf;
+            int pos = e0;
+            while (pos < e1 && s.idx[pos] < ks) ++pos;
+            const int n_before = s.n;
+            if (!support_set<T>(s, pos, ks, nbs)) {
+                overflow = true;
+                return maxd;
+            }
+            e1 += s.n - n_before;
+            if (lane == f) {
+#pragma unroll
+                for (int u = 0; u < SCAN_V; ++u)
+                    if (u == tf) bv[u] = nbs;
+            }
+            maxd = fmax(maxd, fabs(delta));
+            ++moves;
+            cs.dsum += fabsf((float)delta);
+            ++cs.nmoves;
+            // rank-1 update of the rest of this chunk's slice
+            if (in) {
+                T r[SCAN_V];
+                load4g<T>(a.SC + (size_t)ks * ldp + k0, r);
+#pragma unroll
+                for (int t = 0; t < SCAN_V; ++t) acc[t] = fma(-delta, r[t], acc[t]);
+            }
+            cursor = ks + 1;
+            if (cursor >= cb + CHUNK) break;
+        }
+        if constexpr (STD) {
+            float mx = 0.f;
+#pragma unroll
+            for (int t = 0; t < SCAN_V; ++t) {
+                const int k = k0 + t;
+                if (k < p && k != j && bv[t] == T(0)) mx = fmaxf(mx, fabsf((float)acc[t]));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+            if (lane == 0) cs.ci[ci] = ChunkInfo{mx, cs.dsum, cs.nmoves, e1 - e0};
+            __syncwarp();
+        }
+    }
+    return maxd;
+}
+
+// sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the sorted support (Eq. (14)).
+template <typename T>
+__device__ double residual_quadratic_form_list(int j, const Support<T>& s, const CDArgs<T>& a) {
+    const int lane = threadIdx.x & 31;
+    const int n = s.n;
+    double lin = 0.0, quad = 0.0;
+    for (int t = lane; t < n; t += 32)
+        lin += (double)s.val[t] * (double)a.SC[(size_t)s.idx[t] * a.ldp + j];
+    for (int t = lane; t < n * n; t += 32) {
+        const int u = t / n, v = t % n;
+        quad += (double)s.val[u] * (double)s.val[v] *
+                (double)a.SC[(size_t)s.idx[u] * a.ldp + s.idx[v]];
+    }
+    lin = warp_sum(lin);
+    quad = warp_sum(quad);
+    return (double)a.SC[(size_t)j * a.ldp + j] - 2.0 * lin + quad;
+}
+
+// Algorithm 1 for column j with the lazy gradient.  Returns false when the
+// support outgrew the list (nothing written; the caller queues the column
+// for the eager solver).
+template <typename T, bool STD>
+__device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a, ColCounters& cnt) {
+    const int lane = threadIdx.x & 31;
+    Support<T> s;
+    s.idx = reinterpret_cast<int*>(wsm);
+    s.val = reinterpret_cast<T*>(wsm + LAZY_CAP * sizeof(int));
+    s.n = 0;
+    ColScan cs{reinterpret_cast<ChunkInfo*>(wsm + LAZY_CAP * (sizeof(int) + sizeof(T))), 0.f, 0u};
+    reset_chunks(cs, a.ldp);
+    __syncwarp();
+
+    double sigma = 1.0;                                  // sigma^(0) = 1, b = 0
+    const unsigned long long sweeps0 = cnt.sweeps;
+    const double floor2 = 1e-12 * (double)a.SC[(size_t)j * a.ldp + j];
+    int status = COL_OK;
+    bool overflow = false;
+    int r;
+    for (r = 0; r < a.maxit; ++r) {
+        const T lam = (T)(sigma * a.lambda0);
+        bool inner_ok = false;
+        for (int m = 0; m < a.maxit; ++m) {
+            const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow);
+            ++cnt.sweeps;
+            if (overflow) return false;
+            if ((double)md < a.tol) {
+                inner_ok = true;
+                break;
+            }
+        }
+        if (!inner_ok) status |= COL_NOT_CONVERGED;
+        double q = residual_quadratic_form_list<T>(j, s, a);
+        if (q <= floor2) {
+            q = floor2;
+            status |= COL_DEGENERATE;
+        }
+        const double sn = sqrt(q);
+        const double ds = fabs(sn - sigma);
+        sigma = sn;
+        if (ds < a.tol) break;
+    }
+    if (r == a.maxit) {
+        r = a.maxit - 1;
+        status |= COL_NOT_CONVERGED;
+    }
+    // b_j into row j of BT (zeroed before the fit)
+    T* brow = a.BT + (size_t)j * a.ldp;
+    for (int t = lane; t < s.n; t += 32) brow[s.idx[t]] = s.val[t];
+    if (lane == 0) {
+        a.sigma[j] = sigma;
+        a.col_status[j] = status;
+    }
+    cnt.outer_max = max(cnt.outer_max, r + 1);
+    cnt.max_sw = max(cnt.max_sw, (int)(cnt.sweeps - sweeps0));
+    cnt.n_nc += (status & COL_NOT_CONVERGED) != 0;
+    cnt.n_deg += (status & COL_DEGENERATE) != 0;
+    __syncwarp();
+    return true;
 }
 
 // One 32 x 32 tile (rows j0.., columns k0..) of Theta: Omega_1 = -B D on the

@@ -39,7 +39,9 @@ struct FitCtrl {
     unsigned long long nnz;            // nonzero b at exit
     int inner_cap_hit;                 // joint rule: inner cap reached in some outer iteration
     int max_col_sweeps;                // largest per-column sweep count
-    int pad[6];
+    int ovf_count;                     // columns handed from the lazy to the eager solver
+    int ovf_next;                      // eager solver's position in that queue
+    int pad[4];
 };
 static_assert(sizeof(FitCtrl) <= 256, "FitCtrl must fit its 256-byte slot");
 
@@ -111,6 +113,7 @@ struct FitLaunch {
     double* sigma_out;
     unsigned char* ws;   // workspace base
     cudaEvent_t* phase_events;   // nullptr, or 3 events: before CD, after CD, after Theta
+    int gradient;                // spmesl_gradient (column rule only)
 };
 cudaError_t launch_fit(const FitLaunch& f, cudaStream_t st);
 cudaError_t launch_export_B(const unsigned char* ws, int p, int precision, double* B,

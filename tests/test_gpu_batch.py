@@ -21,9 +21,9 @@ import paper_2203_15031_gb300 as sp  # noqa: E402
 DEV = torch.device("cuda", 0)
 
 
-def _single(X, lam, prec, tol, maxit=1000):
+def _single(X, lam, prec, tol, maxit=1000, gradient=0):
     S = sp.gram(X, precision=prec)
-    T, sg, st = sp.fit(S, lam, tol=tol, maxit=maxit, precision=prec)
+    T, sg, st = sp.fit(S, lam, tol=tol, maxit=maxit, precision=prec, gradient=gradient)
     return T.cpu().numpy(), sg.cpu().numpy(), st
 
 
@@ -37,15 +37,16 @@ SMALL = [dict(kind="er", p=37, n=20, seed=1), dict(kind="ar1", p=200, n=90, seed
          dict(kind="ar1", p=2, n=10, seed=5), dict(kind="er", p=64, n=7, seed=6)]
 
 
+@pytest.mark.parametrize("gradient", [sp.GRADIENT_AUTO, sp.GRADIENT_EAGER])
 @pytest.mark.parametrize("prec,dt,tol", [("fp32", np.float32, 1e-6), ("fp64", np.float64, 1e-9)])
-def test_batch_equals_single_fits_and_oracle(prec, dt, tol):
+def test_batch_equals_single_fits_and_oracle(prec, dt, tol, gradient):
     probs, inputs = _problems(SMALL, dt)
-    bt = sp.Batch(inputs, kind="X", precision=prec, tol=tol)
+    bt = sp.Batch(inputs, kind="X", precision=prec, tol=tol, gradient=gradient)
     bt.run()
     statuses, st = bt.result()
     assert all(s == sp.SPMESL_OK for s in statuses), statuses
     for i, (pr, (X, lam)) in enumerate(zip(probs, inputs)):
-        T1, s1, _ = _single(X, lam, prec, tol)
+        T1, s1, _ = _single(X, lam, prec, tol, gradient=gradient)
         Tb, sb = bt.Theta[i].cpu().numpy(), bt.sigma[i].cpu().numpy()
         assert np.array_equal(Tb, T1) and np.array_equal(sb, s1), i
         ref = oracle.spmesl(oracle.gram(pr.X.astype(np.float64)), lam, tol=tol, maxit=1000)

@@ -185,3 +185,39 @@ def test_er_p2000_n200_fp32_full():
         if inner == sp.INNER_COLUMN:
             Sref, ref = _oracle_fit(prob.X, prob.lambda0, w["tol"], w["maxit"])
         _assert_parity(T, ref)
+
+
+# ---------------------------------------------------------------------------- gradient modes
+@pytest.mark.parametrize("gradient", [sp.GRADIENT_EAGER, sp.GRADIENT_LAZY])
+@pytest.mark.parametrize("prec,standardize", [("fp32", True), ("fp64", True), ("fp32", False)])
+def test_gradient_modes_match_oracle(gradient, prec, standardize):
+    dt = np.float64 if prec == "fp64" else np.float32
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    prob = synth.make_problem("hub_scaled", 300, 140, 17, dtype=dt)
+    Xd = torch.from_numpy(prob.X).to(DEV)
+    S = sp.gram(Xd, precision=prec)
+    T, sg, st = sp.fit(S, prob.lambda0, tol=tol, maxit=2000, precision=prec, gradient=gradient,
+                       standardize=standardize)
+    assert st["status"] == sp.SPMESL_OK
+    _, ref = _oracle_fit(prob.X, prob.lambda0, tol, 2000, standardize=standardize)
+    _assert_parity(T.cpu().numpy(), ref)
+
+
+def test_lazy_support_overflow_falls_back_to_eager():
+    """A tiny penalty with n >> p makes supports of ~p-1 > 512 entries: those
+    columns leave the lazy solver's list and are solved again by the eager
+    solver; the fit must still match the oracle."""
+    prob = synth.make_problem("ar1", 700, 2800, 21, dtype=np.float32)
+    lam = 0.0005
+    Xd = torch.from_numpy(prob.X).to(DEV)
+    S = sp.gram(Xd, precision="fp32")
+    Ta, sa, sta, Ba = sp.fit(S, lam, tol=1e-6, maxit=5000, precision="fp32",
+                             gradient=sp.GRADIENT_AUTO, return_B=True)
+    # some column's support exceeds the lazy list, so the fallback really ran
+    assert int((Ba != 0).sum(dim=0).max()) > 512
+    Te, se, ste = sp.fit(S, lam, tol=1e-6, maxit=5000, precision="fp32",
+                         gradient=sp.GRADIENT_EAGER)
+    assert sta["status"] == sp.SPMESL_OK and ste["status"] == sp.SPMESL_OK
+    _, ref = _oracle_fit(prob.X, lam, 1e-6, 5000)
+    _assert_parity(Ta.cpu().numpy(), ref)
+    _assert_parity(Te.cpu().numpy(), ref)
