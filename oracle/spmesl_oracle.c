@@ -57,6 +57,9 @@ void oracle_gram(const double* X, int n, int p, int center, double* S)
             for (int k = 0; k < p; ++k) mu[k] += X[(size_t)i * p + k];
         for (int k = 0; k < p; ++k) mu[k] /= (double)n;
     }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
     for (int k = 0; k < p; ++k) {
         for (int l = k; l < p; ++l) {
             double acc = 0.0;

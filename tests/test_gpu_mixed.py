@@ -1,0 +1,96 @@
+"""Mixed precision: split-BF16 Gram on the tensor cores (tcgen05, TMEM
+accumulators, TMA operand loads) and the FP32 coordinate descent on its S,
+against the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from checks import compare_theta
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2203_15031_gb300 as sp  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.mark.parametrize("n,p", [(75, 130), (1, 3), (64, 128), (200, 300), (500, 257), (129, 1000)])
+@pytest.mark.parametrize("center", [False, True])
+def test_split_bf16_gram_matches_fp64(n, p, center):
+    rng = np.random.default_rng(n + 7 * p)
+    X = (rng.standard_normal((n, p)) + (0.3 if center else 0.0)).astype(np.float32)
+    S = sp.gram(torch.from_numpy(X).to(DEV), precision="mixed", center=center).cpu().numpy()
+    ref = oracle.gram(X.astype(np.float64), center=center)
+    assert np.isfinite(S).all()
+    assert np.array_equal(S, S.T)
+    scale = float(np.max(np.abs(ref)))
+    # dropped lo*lo term and split residual: ~2^-17 of each product
+    assert float(np.max(np.abs(S - ref))) <= 2e-5 * scale
+
+
+def test_mixed_fit_small():
+    prob = synth.make_problem("hub_scaled", 400, 150, 5, dtype=np.float32)
+    S = sp.gram(torch.from_numpy(prob.X).to(DEV), precision="mixed")
+    T, sg, st = sp.fit(S, prob.lambda0, tol=1e-6, precision="mixed")
+    assert st["status"] == sp.SPMESL_OK
+    ref = oracle.spmesl(oracle.gram(prob.X.astype(np.float64)), prob.lambda0, tol=1e-6,
+                        nthreads=0)
+    res = compare_theta(T.cpu().numpy(), ref["Theta"], ref["B"], ref["sigma"])
+    assert res["ok"], res
+
+
+def test_hub_p10000_n500_mixed_full_size_sampled():
+    """Full-size workload (hub network, p = 10000, n = 500, split-BF16 Gram,
+    FP32 coordinate descent, FP64 sigma / Theta), checked on a sample of
+    columns the oracle solves one by one: every hub plus random columns."""
+    w = synth.WORKLOADS["hub_p10000_n500_mixed"]
+    prob = synth.make_problem("hub", 10000, 500, 0, dtype=np.float32)
+    X = torch.from_numpy(prob.X).to(DEV)
+    S = sp.gram(X, precision="mixed")
+    T, sg, st, B = sp.fit(S, prob.lambda0, tol=w["tol"], maxit=w["maxit"], precision="mixed",
+                          return_B=True)
+    assert st["status"] == sp.SPMESL_OK, st
+    Sref = oracle.gram(prob.X.astype(np.float64))
+    # Gram parity on a sampled block and the diagonal
+    Sg = S.cpu().numpy()
+    scale = float(np.abs(np.diag(Sref)).max())
+    rng = np.random.default_rng(1)
+    rows = rng.choice(10000, 64, replace=False)
+    assert float(np.max(np.abs(Sg[rows] - Sref[rows]))) <= 2e-5 * scale
+    # columns: the hubs (largest degree in theta) and random ones
+    deg = (prob.theta != 0).sum(0)
+    hubs = np.argsort(-deg)[:20]
+    cols = np.unique(np.concatenate([hubs, rng.choice(10000, 44, replace=False)]))
+    ref = oracle.columns(Sref, cols, prob.lambda0, tol=w["tol"], maxit=w["maxit"], nthreads=0)
+    assert ref["worst"] == oracle.COL_OK
+    Bg = B.cpu().numpy()
+    sgm = sg.cpu().numpy()
+    Tg = T.cpu().numpy()
+    tmax = float(np.max(np.abs(np.diag(Tg))))
+    tol = 1e-4 * tmax
+    for t, k in enumerate(cols):
+        # sigma and the unsymmetrised column k of Omega_1 = -b_k / sigma_k^2
+        assert abs(sgm[k] - ref["sigma"][t]) <= 1e-4 * ref["sigma"][t]
+        col_gpu = -Bg[:, k] / sgm[k] ** 2
+        col_ref = -ref["b"][t] / ref["sigma"][t] ** 2
+        assert float(np.max(np.abs(col_gpu - col_ref))) <= tol, k
+        supp_diff = (col_gpu != 0) != (col_ref != 0)
+        assert not np.any(supp_diff & (np.maximum(np.abs(col_gpu), np.abs(col_ref)) >= 1e-6 * tmax))
+    # symmetrised entries for pairs inside the sample
+    pos = {k: t for t, k in enumerate(cols)}
+    for j in cols:
+        for k in cols:
+            if j >= k:
+                continue
+            a = -ref["b"][pos[k]][j] / ref["sigma"][pos[k]] ** 2     # omega_jk from regression k
+            b = -ref["b"][pos[j]][k] / ref["sigma"][pos[j]] ** 2     # omega_kj from regression j
+            want = a if abs(a) <= abs(b) else b
+            if abs(abs(a) - abs(b)) > tol:
+                assert abs(Tg[j, k] - want) <= tol and Tg[j, k] == Tg[k, j]
