@@ -30,6 +30,7 @@ struct BatchFit {
     void* BT;
     void* diag;
     double* cs;
+    float* csf;
     double* sigma;
     int* col_status;
     double* Theta;
@@ -87,34 +88,24 @@ __global__ void batch_prep_diag_kernel(const BatchFit* __restrict__ fits, int st
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < f.p; j += gridDim.x * blockDim.x) {
         const double d = (double)S[(size_t)j * f.p + j];
         if (!(d > 0.0) || !isfinite(d)) set_error(f.ctrl, DEV_ERR_NONFINITE);
-        f.cs[j] = standardize ? 1.0 / sqrt(d) : 1.0;
+        const double c = standardize ? 1.0 / sqrt(d) : 1.0;
+        f.cs[j] = c;
+        f.csf[j] = (float)c;
         f.sigma[j] = 1.0;
         f.col_status[j] = COL_OK;
     }
 }
 
+// blockIdx.y = fit; blocks stride over the fit's rows (same arithmetic as
+// the single-fit prep_matrix_kernel), clearing BT on the way.
 template <typename T>
 __global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits) {
     const BatchFit& f = fits[blockIdx.y];
-    const T* S = static_cast<const T*>(f.S);
-    T* SC = static_cast<T*>(f.SC);
-    T* BT = static_cast<T*>(f.BT);
-    T* diag = static_cast<T*>(f.diag);
-    const size_t total = (size_t)f.p * f.ldp;
     bool bad = false;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / f.ldp), c = (int)(i % f.ldp);
-        T v = T(0);
-        if (c < f.p) {
-            const T s = S[(size_t)r * f.p + c];
-            bad |= !isfinite((double)s);
-            v = (T)((double)s * f.cs[r] * f.cs[c]);
-            if (c == r) diag[r] = v;
-        }
-        SC[i] = v;
-        BT[i] = T(0);
-    }
+    for (int r = blockIdx.x; r < f.p; r += gridDim.x)
+        bad |= standardize_row<T>(static_cast<const T*>(f.S), f.p, f.ldp, r, f.cs, f.csf,
+                                  static_cast<T*>(f.SC), nullptr, static_cast<T*>(f.BT),
+                                  static_cast<T*>(f.diag), threadIdx.x, blockDim.x);
     if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
 }
 
@@ -231,7 +222,7 @@ struct FitPlan {
     const void* S;
     double* Theta;
     double* sigma;
-    size_t off_ctrl, off_cs, off_sigma, off_status, off_diag, off_mu, off_Sg, off_SC, off_BT;
+    size_t off_ctrl, off_cs, off_csf, off_sigma, off_status, off_diag, off_mu, off_Sg, off_SC, off_BT;
     int col_start, gram_start, theta_start;
 };
 
@@ -316,7 +307,8 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     }
     batch_prep_diag_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits,
                                                                                    b->standardize);
-    const int mx = std::max(1, std::min(64, (int)(((size_t)b->max_p * b->max_ldp + 8191) / 8192)));
+    // rows per fit spread over blocks; enough blocks overall to fill the GPU
+    const int mx = std::max(1, std::min(b->max_p, (num_sms() * 8 + count - 1) / count));
     batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits);
 
     const size_t budget = (size_t)max_smem_block() - 1024;
@@ -395,6 +387,7 @@ void stage_table(spmesl_batch* b, unsigned char* ws) {
         d.BT = ws + f.off_BT;
         d.diag = ws + f.off_diag;
         d.cs = reinterpret_cast<double*>(ws + f.off_cs);
+        d.csf = reinterpret_cast<float*>(ws + f.off_csf);
         d.sigma = reinterpret_cast<double*>(ws + f.off_sigma);
         d.col_status = reinterpret_cast<int*>(ws + f.off_status);
         d.Theta = f.Theta;
@@ -490,6 +483,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
         const size_t mat = align_up((size_t)f.p * f.ldp * s, 256);
         f.off_ctrl = b->off_ctrls + (size_t)256 * k;
         f.off_cs = off;     off += align_up((size_t)f.p * 8, 256);
+        f.off_csf = off;    off += align_up((size_t)f.p * 4, 256);
         f.off_sigma = off;  off += align_up((size_t)f.p * 8, 256);
         f.off_status = off; off += align_up((size_t)f.p * 4, 256);
         f.off_diag = off;   off += align_up((size_t)f.p * s, 256);

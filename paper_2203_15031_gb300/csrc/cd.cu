@@ -271,11 +271,14 @@ __global__ void __launch_bounds__(512) cd_joint_kernel(CDArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void prep_diag_kernel(const T* __restrict__ S, int p, int standardize, double* cs,
-                                 double* sigma, int* active, int* col_status, FitCtrl* ctrl) {
+                                 float* csf, double* sigma, int* active, int* col_status,
+                                 FitCtrl* ctrl) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x) {
         const double d = (double)S[(size_t)j * p + j];
         if (!(d > 0.0) || !isfinite(d)) set_error(ctrl, DEV_ERR_NONFINITE);
-        cs[j] = standardize ? 1.0 / sqrt(d) : 1.0;
+        const double c = standardize ? 1.0 / sqrt(d) : 1.0;
+        cs[j] = c;
+        csf[j] = (float)c;
         sigma[j] = 1.0;
         active[j] = j;
         col_status[j] = COL_OK;
@@ -283,24 +286,15 @@ __global__ void prep_diag_kernel(const T* __restrict__ S, int p, int standardize
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->n_active = p;
 }
 
+// One block per row of S^C (grid-stride over rows).
 template <typename T>
 __global__ void prep_matrix_kernel(const T* __restrict__ S, int p, int ldp, const double* cs,
-                                   T* SC, T* GT, T* diag, int init_g, FitCtrl* ctrl) {
-    const size_t total = (size_t)p * ldp;
+                                   const float* csf, T* SC, T* GT, T* diag, int init_g,
+                                   FitCtrl* ctrl) {
     bool bad = false;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / ldp), c = (int)(i % ldp);
-        T v = T(0);
-        if (c < p) {
-            const T s = S[(size_t)r * p + c];
-            bad |= !isfinite((double)s);
-            v = (T)((double)s * cs[r] * cs[c]);
-            if (c == r) diag[r] = v;
-        }
-        SC[i] = v;
-        if (init_g) GT[i] = v;
-    }
+    for (int r = blockIdx.x; r < p; r += gridDim.x)
+        bad |= standardize_row<T>(S, p, ldp, r, cs, csf, SC, init_g ? GT : nullptr, nullptr,
+                                  diag, threadIdx.x, blockDim.x);
     if (bad) set_error(ctrl, DEV_ERR_NONFINITE);
 }
 
@@ -406,14 +400,13 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     const int pb = 256;
     prep_diag_kernel<T><<<(f.p + pb - 1) / pb, pb, 0, st>>>(
         reinterpret_cast<const T*>(f.S), f.p, f.standardize, reinterpret_cast<double*>(ws + L.cs),
-        a.sigma, a.active, a.col_status, ctrl);
+        reinterpret_cast<float*>(ws + L.csf), a.sigma, a.active, a.col_status, ctrl);
     {
-        const size_t total = (size_t)f.p * L.ldp;
-        int grid = (int)std::min<size_t>((total + pb - 1) / pb, (size_t)g_num_sms * 16);
+        const int grid = std::min(f.p, g_num_sms * 8);
         prep_matrix_kernel<T><<<grid, pb, 0, st>>>(
             reinterpret_cast<const T*>(f.S), f.p, L.ldp, reinterpret_cast<double*>(ws + L.cs),
-            reinterpret_cast<T*>(ws + L.SC), a.GT, reinterpret_cast<T*>(ws + L.diag), joint ? 1 : 0,
-            ctrl);
+            reinterpret_cast<const float*>(ws + L.csf), reinterpret_cast<T*>(ws + L.SC), a.GT,
+            reinterpret_cast<T*>(ws + L.diag), joint ? 1 : 0, ctrl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 

@@ -325,6 +325,37 @@ __device__ double residual_quadratic_form(int j, const T* __restrict__ b, const 
     return (double)a.SC[(size_t)j * a.ldp + j] - 2.0 * lin + quad;
 }
 
+// Row r of S^C = C S C into SC (zero padding up to ldp), optionally copied
+// into GT, with BT's row cleared.  FP32 data is scaled in FP32 by the scales
+// rounded once to FP32 (csf); FP64 data in FP64.  Threads tid, tid + nthr, ...
+// of the row.  Returns true if a non-finite entry was seen.
+template <typename T>
+__device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, int ldp, int r,
+                                                const double* __restrict__ cs,
+                                                const float* __restrict__ csf,
+                                                T* __restrict__ SC, T* __restrict__ GT,
+                                                T* __restrict__ BT, T* __restrict__ diag, int tid,
+                                                int nthr) {
+    bool bad = false;
+    const T cr = sizeof(T) == 4 ? (T)csf[r] : (T)cs[r];
+    const T* __restrict__ srow = S + (size_t)r * p;
+    T* __restrict__ out = SC + (size_t)r * ldp;
+    for (int c = tid; c < ldp; c += nthr) {
+        T v = T(0);
+        if (c < p) {
+            const T s = srow[c];
+            bad |= !isfinite(s);
+            const T cc = sizeof(T) == 4 ? (T)csf[c] : (T)cs[c];
+            v = s * cr * cc;
+            if (c == r) diag[r] = v;
+        }
+        out[c] = v;
+        if (GT) GT[(size_t)r * ldp + c] = v;
+        if (BT) BT[(size_t)r * ldp + c] = T(0);
+    }
+    return bad;
+}
+
 // Per-warp counters of the column solves, flushed into a fit's FitCtrl.
 struct ColCounters {
     unsigned long long sweeps = 0, moves = 0;

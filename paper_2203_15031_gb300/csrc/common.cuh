@@ -57,7 +57,7 @@ inline int padded_ld(int p) { return (p + 31) / 32 * 32; }
 // Byte offsets of the fit workspace (see spmesl_fit_workspace_bytes).
 struct FitLayout {
     int ldp;
-    size_t ctrl, cs, sigma, col_status, active, active_next, flag, diag, SC, BT, GT, total;
+    size_t ctrl, cs, csf, sigma, col_status, active, active_next, flag, diag, SC, BT, GT, total;
 };
 
 inline FitLayout fit_layout(int p, int precision) {
@@ -68,6 +68,7 @@ inline FitLayout fit_layout(int p, int precision) {
     size_t off = 0;
     L.ctrl = off;        off += 256;
     L.cs = off;          off += align_up((size_t)p * 8, 256);
+    L.csf = off;         off += align_up((size_t)p * 4, 256);
     L.sigma = off;       off += align_up((size_t)p * 8, 256);
     L.col_status = off;  off += align_up((size_t)p * 4, 256);
     L.active = off;      off += align_up((size_t)p * 4, 256);
