@@ -10,9 +10,11 @@ launch per phase for all ten fits.  The plain path (one spmesl_gram +
 spmesl_fit per fit, serialised on one stream) is timed beside it.
 
 JSON line fields beyond the base contract:
-  e2e          the same metric through spmesl_solve with HOST buffers (X copied
-               in, Theta and sigma copied out, inside the timed region)
-  roofline     the coordinate-descent kernel: algorithmic bytes per launch over
+  e2e          the same metric through the batched C ABI with HOST buffers (the
+               ten X copied in from pinned memory, every Theta and sigma copied
+               out, inside the timed region)
+  plain        solves/s of the one-fit-per-launch path on the same ten datasets
+  roofline     the coordinate-descent launch: algorithmic bytes per launch over
                its CUDA-event duration, against the measured HBM copy bandwidth
   cpu_baseline the FP64 oracle on the host cores, on a bounded sample
   latency      p50 / p99 of the per-solve device time
@@ -39,7 +41,7 @@ if ROOT not in sys.path:
 METRIC = "SPMESL solves/s + p99 latency, mixed-prec batched vs plain GPU @ dTheta<=1e-4"
 WORKLOAD = "er_p2000_n200_fp32"
 N_DATASETS = 10
-KERNELS_PER_SOLVE = 5        # per batched step: gram, prep_diag, prep_matrix, cd, theta
+KERNELS_PER_SOLVE = 6        # per batched step: gram, prep_diag, prep_matrix, lazy cd, eager cd queue, theta
 
 
 def _env_rank():
@@ -171,7 +173,7 @@ def _sha_of(paths):
 
 
 CD_SOURCES = ["paper_2203_15031_gb300/csrc/cd_device.cuh", "paper_2203_15031_gb300/csrc/batch.cu"]
-PROFILE = "profiles/batch_cd_kernel_er_p2000_n200_x10.md"
+PROFILE = "profiles/batch_cd_lazy_kernel_er_p2000_n200_x10.md"
 
 
 def measured_traffic():
@@ -327,7 +329,7 @@ def run_ours(args):
         traffic = measured_traffic()
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
-                "kernel": "batch_cd_kernel<float,1>", "peak_kind": which,
+                "kernel": "batch_cd_lazy_kernel<float,1>", "peak_kind": which,
                 "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cd_mean_ms,
                 "moves_per_launch": mv, "warps_per_block": best_w}
         srt = sorted(per)
@@ -360,6 +362,112 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_single(args):
+    """One whole solve per step (Gram + fit) of a single-fit workload, e.g.
+    the hub network p = 10000, n = 500 with the split-BF16 tensor-core Gram.
+    Reports the coordinate-descent roofline (dominant kernel) and the Gram's
+    tensor roofline."""
+    import numpy as np
+    import torch
+
+    import paper_2203_15031_gb300 as sp
+    import synth
+
+    rank, local_rank, world = _env_rank()
+    if world > 1:
+        raise SystemExit("--workload other than the default runs on one GPU")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sp.lib()
+    w = synth.WORKLOADS[args.workload]
+    prec = {"fp64": sp.FP64, "fp32": sp.FP32, "mixed": sp.MIXED}[w["prec"]]
+    dt = np.float64 if prec == sp.FP64 else np.float32
+    prob = synth.make_problem(w["kind"], w["p"], w["n"], 0, dtype=dt)
+    p, n, tol, maxit = w["p"], w["n"], w["tol"], w["maxit"]
+    X = torch.from_numpy(prob.X).to(dev)
+    S = torch.empty((p, p), dtype=X.dtype, device=dev)
+    Theta = torch.empty((p, p), dtype=torch.float64, device=dev)
+    sigma = torch.empty(p, dtype=torch.float64, device=dev)
+    gnb = sp.spmesl_gram_workspace_bytes(n, p, prec)
+    fnb = sp.spmesl_fit_workspace_bytes(p, prec)
+    gkeep, gws = sp._workspace(max(gnb, 1), dev)
+    fkeep, fws = sp._workspace(fnb, dev)
+    opts = sp.spmesl_default_opts()
+    opts.precision = prec
+    opts.record_phase_times = 1
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        g0.record(stream)
+        sp._check(sp.spmesl_gram(X, n, p, p, prec, 0, S, p, gws, gnb, stream), "spmesl_gram")
+        g1.record(stream)
+        sp._check(sp.spmesl_fit(S, n, p, prob.lambda0, tol, maxit, opts, Theta, sigma, None, fws,
+                                fnb, stream), "spmesl_fit")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = sp.Stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    gram_ms, cd_ms, moves = [], [], []
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            sp._check(sp.spmesl_fit_result(fws, p, prec, st, stream), "spmesl_fit_result")
+            gram_ms.append(g0.elapsed_time(g1))
+            cd_ms.append(st.ms_cd)
+            moves.append(st.moves)
+        torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    value = args.steps / (sum(per) / 1e3)
+    hbm, which = _peaks()
+    ldp = (p + 31) // 32 * 32
+    s = 8 if prec == sp.FP64 else 4
+    mv = statistics.mean(moves)
+    bytes_cd = float(s) * ldp * (2 * p + mv)
+    cdm = statistics.mean(cd_ms)
+    roof = {"bound": "hbm", "achieved": bytes_cd / (cdm / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": bytes_cd / (cdm / 1e3) / 1e9 / hbm, "traffic": None,
+            "kernel": "cd_column_lazy_kernel", "peak_kind": which,
+            "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cdm, "moves_per_launch": mv}
+    gm = statistics.mean(gram_ms)
+    roof_gram = None
+    if prec == sp.MIXED:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        t = (p + 127) // 128
+        npad = (n + 63) // 64 * 64
+        executed = 3.0 * (t * (t + 1) // 2) * 128 * 128 * npad * 2
+        roof_gram = {"bound": "tensor", "achieved": executed / (gm / 1e3) / 1e12, "peak": bf16,
+                     "unit": "TFLOP/s", "frac": executed / (gm / 1e3) / 1e12 / bf16,
+                     "kernel": "gram_tc_kernel (+ split_transpose_kernel)",
+                     "executed_mma_flops": executed, "algorithmic_flops": float(n) * p * (p + 1),
+                     "mean_ms": gm, "peak_kind": "measured bf16 burst"}
+    srt = sorted(per)
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(per) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == sp.FP64 else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "p": p, "n": n, "network": w["kind"],
+                       "precision": w["prec"], "tol": tol, "maxit": maxit,
+                       "path": "single fit (spmesl_gram + spmesl_fit)",
+                       "l2": "flushed between steps (256 MB write)"},
+            "latency": {"p50_ms": statistics.median(per),
+                        "p99_ms": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]},
+            "roofline": roof, "roofline_gram": roof_gram,
+            "gpu_launches": ((2 if prec == sp.MIXED else 1) + 5) * args.steps,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    del gkeep, fkeep
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,11 +475,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="default: the batched ER p=2000 line; other names in synth.WORKLOADS "
+                         "run single fits (measurement and profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != WORKLOAD:
+        run_single(args)
     else:
         run_ours(args)
 
