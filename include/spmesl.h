@@ -118,7 +118,10 @@ typedef struct {
     float ms_theta;             /* Theta assembly kernel alone (record_phase_times), ms */
     int32_t max_col_sweeps;     /* largest number of sweeps any one column ran */
     int32_t max_col_outer;      /* largest number of sigma iterations any one column ran */
-    int64_t reserved[2];
+    float ms_queue;             /* serving: submit -> admitted into a batch, ms (host clock) */
+    float ms_total;             /* serving: submit -> completion seen by the context, ms */
+    int32_t batch_size;         /* serving: requests in the batch this one ran in */
+    int32_t reserved32;
 } spmesl_stats;
 
 /* Fill `opts` with the defaults: FP32, standardize = 1, center = 0,
@@ -307,6 +310,42 @@ spmesl_status spmesl_batch_tune(spmesl_batch* batch, void* workspace, size_t ws_
 
 /* Release the batch's host resources (pinned staging, captured graph). */
 void spmesl_batch_destroy(spmesl_batch* batch);
+
+/*
+ * Serving context: continuous batching of requests that arrive over time.
+ * A worker thread admits queued requests in arrival order while the device
+ * bytes of all admitted requests stay within `mem_budget_bytes` and at most
+ * `max_slots` requests are admitted.  The requests of one admission round run
+ * as one batch (as spmesl_batch_run) on one of the context's streams;
+ * requests that arrive while earlier batches run are admitted into new
+ * batches on other streams, so their work overlaps on the device.  A result
+ * does not depend on what it was batched with.  The paper has no serving
+ * system; each request is the fit of Algorithm 2.
+ *
+ * spmesl_ctx_create: tol / maxit apply to every request; opts: precision FP64
+ *   or FP32 (inner_rule COLUMN), other fields as for spmesl_batch_create.
+ *   Uses the current device.  Errors: EINVAL, ENOMEM, ECUDA.
+ * spmesl_submit: `request` (an spmesl_problem: device pointers that must stay
+ *   valid until the request completes; lambda0 <= 0 applies opts->lambda_rule)
+ *   is queued and *ticket receives its id.  EINVAL for a bad request, ENOMEM
+ *   if the request alone exceeds the budget, EBUSY if the queue is full.
+ * spmesl_poll: the request's status once it has completed (its Theta and
+ *   sigma are then written, and stats gets ms_queue / ms_total / batch_size);
+ *   EBUSY while it is queued or running; ENOTFOUND for an unknown ticket or
+ *   one already reported.
+ * spmesl_ctx_query: queued and admitted request counts and the device bytes
+ *   admitted requests hold.
+ * spmesl_ctx_destroy: waits for the batches in flight, then frees the
+ *   context; requests still queued are dropped.
+ */
+typedef struct spmesl_ctx spmesl_ctx;
+spmesl_status spmesl_ctx_create(spmesl_ctx** ctx, size_t mem_budget_bytes, int max_slots,
+                                double tol, int maxit, const spmesl_opts* opts);
+spmesl_status spmesl_submit(spmesl_ctx* ctx, const spmesl_problem* request, uint64_t* ticket);
+spmesl_status spmesl_poll(spmesl_ctx* ctx, uint64_t ticket, spmesl_stats* stats);
+spmesl_status spmesl_ctx_query(spmesl_ctx* ctx, int32_t* queued, int32_t* running,
+                               size_t* bytes_in_use);
+void spmesl_ctx_destroy(spmesl_ctx* ctx);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,8 @@ __all__ = [
     "spmesl_solve_workspace_bytes",
     "spmesl_solve", "spmesl_batch_create", "spmesl_batch_workspace_bytes", "spmesl_batch_run",
     "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_destroy", "Problem", "Batch",
+    "spmesl_ctx_create", "spmesl_submit", "spmesl_poll", "spmesl_ctx_query", "spmesl_ctx_destroy",
+    "Server",
     "gram", "fit", "solve",
 ]
 
@@ -63,10 +65,12 @@ class Stats(ctypes.Structure):
                 ("lambda0", ctypes.c_double), ("ms_gram", ctypes.c_float),
                 ("ms_fit", ctypes.c_float), ("ms_cd", ctypes.c_float),
                 ("ms_theta", ctypes.c_float), ("max_col_sweeps", ctypes.c_int32),
-                ("max_col_outer", ctypes.c_int32), ("reserved", ctypes.c_int64 * 2)]
+                ("max_col_outer", ctypes.c_int32), ("ms_queue", ctypes.c_float),
+                ("ms_total", ctypes.c_float), ("batch_size", ctypes.c_int32),
+                ("reserved32", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
 
 
 class SpmeslError(RuntimeError):
@@ -101,6 +105,13 @@ _SIGS = {
                                    ctypes.POINTER(Stats), _vp]),
     "spmesl_batch_tune": (_i32, [_vp, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_int)]),
     "spmesl_batch_destroy": (None, [_vp]),
+    "spmesl_ctx_create": (_i32, [ctypes.POINTER(ctypes.c_void_p), _sz, _i32, _dbl, _i32,
+                                 ctypes.POINTER(Opts)]),
+    "spmesl_submit": (_i32, [_vp, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_uint64)]),
+    "spmesl_poll": (_i32, [_vp, ctypes.c_uint64, ctypes.POINTER(Stats)]),
+    "spmesl_ctx_query": (_i32, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_size_t)]),
+    "spmesl_ctx_destroy": (None, [_vp]),
     "spmesl_solve_workspace_bytes": (_sz, [_i32, _i32, _i32]),
     "spmesl_solve": (_i32, [_vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts), _vp, _vp,
                             ctypes.POINTER(Stats), _vp, _sz, _vp]),
@@ -391,6 +402,94 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             spmesl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spmesl_ctx_create(mem_budget_bytes, max_slots, tol, maxit, opts):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().spmesl_ctx_create(ctypes.byref(h), mem_budget_bytes, max_slots, tol, maxit,
+                                 ctypes.byref(opts) if opts is not None else None)
+    return rc, h.value
+
+
+def spmesl_submit(ctx, request: Problem):
+    """Returns (status, ticket)."""
+    t = ctypes.c_uint64(0)
+    rc = lib().spmesl_submit(ctx, ctypes.byref(request), ctypes.byref(t))
+    return rc, t.value
+
+
+def spmesl_poll(ctx, ticket, stats=None) -> int:
+    return lib().spmesl_poll(ctx, ticket, ctypes.byref(stats) if stats is not None else None)
+
+
+def spmesl_ctx_query(ctx):
+    q, r, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    rc = lib().spmesl_ctx_query(ctx, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b))
+    return rc, q.value, r.value, b.value
+
+
+def spmesl_ctx_destroy(ctx) -> None:
+    lib().spmesl_ctx_destroy(ctx)
+
+
+class Server:
+    """Owning wrapper of a serving context.  ``submit`` takes a CUDA tensor X
+    (n x p) or S (p x p) and lambda0, allocates the outputs and returns a
+    ticket; ``poll`` returns None while the request runs, else
+    (status, Theta, sigma, stats_dict)."""
+
+    def __init__(self, mem_budget_bytes, max_slots=256, precision="fp32", tol=1e-6, maxit=1000):
+        _require_cuda()
+        opts = spmesl_default_opts()
+        opts.precision = _prec(precision)
+        rc, self.handle = spmesl_ctx_create(int(mem_budget_bytes), int(max_slots), tol, maxit,
+                                            opts)
+        _check(rc, "spmesl_ctx_create")
+        self._live = {}
+
+    def submit(self, tensor, lambda0, kind="X"):
+        import torch
+        t = tensor.contiguous()
+        if kind == "X":
+            n, p = t.shape
+        else:
+            n, p = 0, t.shape[0]
+        Th = torch.empty((p, p), dtype=torch.float64, device=t.device)
+        sg = torch.empty(p, dtype=torch.float64, device=t.device)
+        req = Problem(t.data_ptr() if kind == "X" else None, t.data_ptr() if kind == "S" else None,
+                      n, p, float(lambda0), Th.data_ptr(), sg.data_ptr())
+        # the inputs must be ready before the context's streams read them
+        torch.cuda.current_stream().synchronize()
+        rc, ticket = spmesl_submit(self.handle, req)
+        _check(rc, "spmesl_submit")
+        self._live[ticket] = (t, Th, sg)
+        return ticket
+
+    def poll(self, ticket):
+        st = Stats()
+        rc = spmesl_poll(self.handle, ticket, st)
+        if rc == SPMESL_EBUSY:
+            return None
+        if rc == SPMESL_ENOTFOUND:
+            raise SpmeslError(rc, "spmesl_poll")
+        _, Th, sg = self._live.pop(ticket)
+        return rc, Th, sg, st.as_dict()
+
+    def query(self):
+        _, q, r, b = spmesl_ctx_query(self.handle)
+        return dict(queued=q, running=r, bytes_in_use=b)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spmesl_ctx_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

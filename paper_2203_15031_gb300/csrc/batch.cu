@@ -42,6 +42,8 @@ struct BatchFit {
     int pad[2];
 };
 
+thread_local bool g_batch_pageable_staging = false;
+
 struct BatchHeader {
     int next_col;         // column queue of the first coordinate-descent launch
     int ovf_count;        // columns handed from the lazy to the eager kernel
@@ -270,6 +272,7 @@ struct spmesl_batch {
     bool any_x = false;
     // pinned staging of the descriptor table and the prefix arrays
     unsigned char* pinned = nullptr;
+    bool pinned_is_pageable = false;
     size_t table_bytes = 0;
     const void* table_ws = nullptr;    // workspace the staged table points into
     cudaGraphExec_t graph = nullptr;
@@ -515,7 +518,16 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->off_ovf = off;
     off += align_up(sizeof(int) * (size_t)cols, 256);
     b->ws_bytes = off;
-    if (cudaMallocHost(&b->pinned, b->table_bytes) != cudaSuccess) {
+    if (spmesl::g_batch_pageable_staging) {
+        // used by the serving context: no pinned allocation (whose release can
+        // synchronise the device) per admission round
+        b->pinned = static_cast<unsigned char*>(malloc(b->table_bytes));
+        b->pinned_is_pageable = true;
+        if (!b->pinned) {
+            delete b;
+            return SPMESL_ENOMEM;
+        }
+    } else if (cudaMallocHost(&b->pinned, b->table_bytes) != cudaSuccess) {
         delete b;
         return SPMESL_ENOMEM;
     }
@@ -583,8 +595,9 @@ spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, 
     if (cudaStreamSynchronize(st) != cudaSuccess) return SPMESL_ECUDA;
     const unsigned char* ws = static_cast<const unsigned char*>(workspace);
     std::vector<unsigned char> ctrls((size_t)256 * b->count);
-    if (cudaMemcpy(ctrls.data(), ws + b->off_ctrls, ctrls.size(), cudaMemcpyDeviceToHost) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(ctrls.data(), ws + b->off_ctrls, ctrls.size(), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return SPMESL_ECUDA;
     spmesl_status worst = SPMESL_OK;
     spmesl_stats agg;
@@ -661,7 +674,10 @@ void spmesl_batch_destroy(spmesl_batch* b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
     if (b->ev[1]) cudaEventDestroy(b->ev[1]);
-    if (b->pinned) cudaFreeHost(b->pinned);
+    if (b->pinned) {
+        if (b->pinned_is_pageable) free(b->pinned);
+        else cudaFreeHost(b->pinned);
+    }
     delete b;
 }
 

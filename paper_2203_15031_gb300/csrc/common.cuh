@@ -120,4 +120,9 @@ cudaError_t launch_fit(const FitLaunch& f, cudaStream_t st);
 cudaError_t launch_export_B(const unsigned char* ws, int p, int precision, double* B,
                             cudaStream_t st);
 int max_p_for(int precision);
+
+// When true on the calling thread, spmesl_batch_create stages its descriptor
+// table in ordinary host memory instead of pinned memory (the serving worker
+// sets it: releasing pinned memory can synchronise the whole device).
+extern thread_local bool g_batch_pageable_staging;
 }  // namespace spmesl
