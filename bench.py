@@ -468,6 +468,122 @@ def run_single(args):
     del gkeep, fkeep
 
 
+def run_serve(args):
+    """Serving workload: Poisson arrivals of requests with p log-uniform in
+    [100, 5000], n = max(p/4, 50), networks mixed; continuous batching
+    (spmesl_ctx, 120 GB admission budget) against the plain path (one fit per
+    launch, first-come first-served on one stream), at arrival rates that
+    are fractions of the measured saturation throughput."""
+    import numpy as np
+    import torch
+
+    import paper_2203_15031_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sp.lib()
+    rng = np.random.default_rng(7)
+    kinds = ["ar1", "er", "hub_scaled"]
+    pool = []
+    for i in range(args.serve_pool):
+        p = int(round(math.exp(rng.uniform(math.log(100), math.log(5000)))))
+        n = max(p // 4, 50)
+        pr = synth.make_problem(kinds[i % 3], p, n, 2000 + i, dtype=np.float32)
+        pool.append((torch.from_numpy(pr.X).to(dev), pr.lambda0, p, n))
+    R = args.serve_requests
+    order = rng.integers(0, len(pool), R)
+    tol, maxit = 1e-6, 1000
+
+    def serve_run(rate):
+        srv = sp.Server(120 << 30, max_slots=256, precision="fp32", tol=tol, maxit=maxit)
+        gaps = rng.exponential(1.0 / rate, R) if rate else np.zeros(R)
+        arrivals = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        live, lat, done_t = {}, [], []
+        k = 0
+        while k < R or live:
+            now = time.perf_counter() - t0
+            while k < R and arrivals[k] <= now:
+                X, lam, _, _ = pool[order[k]]
+                live[srv.submit(X, lam)] = k
+                k += 1
+            for t in list(live):
+                r = srv.poll(t)
+                if r is not None:
+                    if r[0] not in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED):
+                        raise RuntimeError(f"request failed: {r[0]}")
+                    lat.append(r[3]["ms_total"])
+                    done_t.append(time.perf_counter() - t0)
+                    del live[t]
+            if not live and k < R:
+                time.sleep(max(0.0, min(0.001, arrivals[k] - (time.perf_counter() - t0))))
+        srv.close()
+        span = max(done_t) - arrivals[0]
+        return R / span, lat
+
+    S = {}
+    ws = {}
+
+    def plain_fit(idx):
+        X, lam, p, n = pool[idx]
+        if p not in S:
+            S[p] = torch.empty((p, p), dtype=torch.float32, device=dev)
+            gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
+            fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
+            ws[p] = (sp._workspace(max(gnb, 1), dev), gnb, sp._workspace(fnb, dev), fnb,
+                     torch.empty((p, p), dtype=torch.float64, device=dev),
+                     torch.empty(p, dtype=torch.float64, device=dev))
+        (gk, gws), gnb, (fk, fws), fnb, Th, sg = ws[p]
+        opts = sp.spmesl_default_opts()
+        opts.precision = sp.FP32
+        sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S[p], p, gws, gnb), "spmesl_gram")
+        sp._check(sp.spmesl_fit(S[p], n, p, lam, tol, maxit, opts, Th, sg, None, fws, fnb),
+                  "spmesl_fit")
+        torch.cuda.current_stream().synchronize()
+
+    def plain_run(rate):
+        gaps = rng.exponential(1.0 / rate, R) if rate else np.zeros(R)
+        arrivals = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        lat, done_t = [], []
+        for k in range(R):
+            now = time.perf_counter() - t0
+            if arrivals[k] > now:
+                time.sleep(arrivals[k] - now)
+            plain_fit(order[k])
+            t = time.perf_counter() - t0
+            lat.append(1e3 * (t - arrivals[k]))
+            done_t.append(t)
+        return R / (max(done_t) - arrivals[0]), lat
+
+    def q(v, f):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(math.ceil(f * len(v))) - 1)]
+
+    for i in range(len(pool)):                # warm both paths (kernels, pools)
+        plain_fit(i)
+    serve_run(0)
+    sat_serve, _ = serve_run(0)               # everything at once
+    sat_plain, _ = plain_run(0)
+    rows = []
+    for frac in args.serve_fracs:
+        rate = frac * sat_serve
+        sv, slat = serve_run(rate)
+        pv, plat = plain_run(rate)
+        rows.append({"arrival_rate": rate, "fraction_of_saturation": frac,
+                     "served": {"solves_per_s": sv, "p50_ms": q(slat, 0.5), "p99_ms": q(slat, 0.99)},
+                     "plain": {"solves_per_s": pv, "p50_ms": q(plat, 0.5), "p99_ms": q(plat, 0.99)}})
+    line = {"metric": METRIC, "workload": "serve",
+            "config": {"requests": R, "datasets": len(pool), "p": "log-uniform [100, 5000]",
+                       "n": "max(p/4, 50)", "networks": "ar1 / er / hub_scaled",
+                       "budget_gb": 120, "max_slots": 256, "precision": "fp32", "tol": tol,
+                       "arrivals": "Poisson, seed 7"},
+            "saturation": {"served_solves_per_s": sat_serve, "plain_solves_per_s": sat_plain},
+            "rates": rows, "unit": "solves/s; latency ms from arrival to completion"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,11 +594,16 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="default: the batched ER p=2000 line; other names in synth.WORKLOADS "
                          "run single fits (measurement and profiling)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-pool", type=int, default=24)
+    ap.add_argument("--serve-fracs", type=float, nargs="+", default=[0.1, 0.5, 0.9, 1.1])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     elif args.workload != WORKLOAD:
         run_single(args)
     else:
