@@ -637,15 +637,18 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
 // sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the sorted support (Eq. (14)).
 template <typename T>
 __device__ double residual_quadratic_form_list(int j, const Support<T>& s, const CDArgs<T>& a) {
+    // Every product b_v S_uv is formed in the data precision (one rounding)
+    // and every sum is carried in FP64; FP64 arithmetic is very slow on this
+    // part, so the per-pair FP64 work is one conversion and one add.
     const int lane = threadIdx.x & 31;
     const int n = s.n;
     double lin = 0.0, quad = 0.0;
-    for (int t = lane; t < n; t += 32)
-        lin += (double)s.val[t] * (double)a.SC[(size_t)s.idx[t] * a.ldp + j];
+    for (int u = lane; u < n; u += 32)
+        lin += (double)(s.val[u] * a.SC[(size_t)s.idx[u] * a.ldp + j]);
+    // pairs spread over the lanes: independent accumulators, short chains
     for (int t = lane; t < n * n; t += 32) {
-        const int u = t / n, v = t % n;
-        quad += (double)s.val[u] * (double)s.val[v] *
-                (double)a.SC[(size_t)s.idx[u] * a.ldp + s.idx[v]];
+        const int u = t / n, v = t - (t / n) * n;
+        quad += (double)(s.val[u] * s.val[v] * a.SC[(size_t)s.idx[u] * a.ldp + s.idx[v]]);
     }
     lin = warp_sum(lin);
     quad = warp_sum(quad);
