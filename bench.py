@@ -442,9 +442,13 @@ def run_single(args):
     if prec == sp.MIXED:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             bf16 = float(json.load(f)["bf16_tflops"])
-        t = (p + 127) // 128
+        # 128 x bn tiles holding an entry of the upper triangle; three MMAs
+        # (hi*hi, hi*lo, lo*hi) over the padded sample dimension per tile
+        bn = 256 if p > 1024 else 128
+        tm_count, tn_count = (p + 127) // 128, (p + bn - 1) // bn
+        tiles = sum(tn_count - (128 * tm) // bn for tm in range(tm_count))
         npad = (n + 63) // 64 * 64
-        executed = 3.0 * (t * (t + 1) // 2) * 128 * 128 * npad * 2
+        executed = 3.0 * tiles * 128 * bn * npad * 2
         roof_gram = {"bound": "tensor", "achieved": executed / (gm / 1e3) / 1e12, "peak": bf16,
                      "unit": "TFLOP/s", "frac": executed / (gm / 1e3) / 1e12 / bf16,
                      "kernel": "gram_tc_kernel (+ split_transpose_kernel)",

@@ -8,20 +8,28 @@
 // transposes X into K-major copies XhT, XlT ([p][n_pad] bf16, n_pad a
 // multiple of 64, zero-padded), so both MMA operands are K-major rows.
 //
-// Main kernel: one CTA (4 warps) per 128 x 128 output tile with tile_m <=
-// tile_n (S is symmetric; the tile and its mirror are both written).
-//   - warp 0, one lane: TMA producer.  Per 64-wide K block it loads the four
-//     128 x 64 bf16 operand tiles (Xh and Xl rows of tile_m and of tile_n)
-//     with 128-byte swizzle into one of 3 shared-memory stages.
-//   - warp 1, one lane: MMA issuer.  Per K block, 4 K-steps of 16, three
-//     tcgen05.mma (hi*hi, hi*lo, lo*hi) into one 128 x 128 FP32 accumulator
-//     in tensor memory; tcgen05.commit frees the stage.
-//   - all 4 warps: epilogue.  Each warp reads its 32 accumulator lanes with
-//     tcgen05.ld, scales by 1/n, stages the tile in shared memory and writes
-//     the tile and its transpose with coalesced stores.
-// Every wait on an mbarrier is bounded; on timeout the CTA stops issuing,
-// writes NaN into its output tile (so the fit that reads S reports
-// non-finite input) and still releases its tensor memory.
+// Main kernel: persistent, one CTA (10 warps) per SM, looping over the
+// 128 x BN output tiles that hold at least one entry of the upper triangle
+// (column >= row); each entry S_jk with k >= j is computed once and written
+// to both S_jk and S_kj, so S is exactly symmetric.
+//   - warp 0, one lane: TMA producer.  Per K block of KB bf16 it loads the
+//     Xh and Xl rows of the tile's 128 rows and BN columns with KB*2-byte
+//     swizzle into one of STAGES shared-memory stages.
+//   - warp 1: owns the tensor memory (two BN-column FP32 accumulators); one
+//     lane issues, per K block and per K step of 16, three tcgen05.mma
+//     (hi*hi, hi*lo, lo*hi) and commits the stage back to the producer and,
+//     after the last K block, the accumulator to the epilogue.
+//   - warps 2-9: epilogue, one 32-lane quadrant of the accumulator and one
+//     half of its columns each.  Per 32-column chunk: tcgen05.ld, scale by
+//     1/n, store the mirror S_kj straight from registers (lanes run along a
+//     row of S) and S_jk as 16-byte stores through a 32 x 32 swizzled
+//     transpose in shared memory.  The accumulator is handed back once
+//     read, so the epilogue of tile i runs under the MMAs of tile i+1.
+// Every wait on an mbarrier is bounded and also ends when another role has
+// failed; on failure the CTA stops issuing, writes NaN into the tile it was
+// on and every later tile of its share (so the fit that reads S reports
+// non-finite input), lets its copies and MMAs in flight land and still
+// releases its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -34,16 +42,34 @@ namespace spmesl {
 
 namespace {
 
-constexpr int TC_TILE = 128;          // M = N = 128
-constexpr int TC_KB = 64;             // K block (64 bf16 = one 128-byte swizzle row)
-constexpr int TC_STAGES = 3;
-constexpr int TC_OP_BYTES = TC_TILE * TC_KB * 2;       // 16 KB per operand tile
-constexpr int TC_STAGE_BYTES = 4 * TC_OP_BYTES;        // Ah, Al, Bh, Bl
-constexpr int TC_TMEM_COLS = 128;
-constexpr int TC_THREADS = 128;
+constexpr int TC_BM = 128;            // accumulator rows = TMEM lanes
+constexpr int TC_THREADS = 320;       // producer, MMA, 8 epilogue warps
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_EPI_WARP0 = 2;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s
-// dynamic shared memory: stages + barriers + 1 KB for 1024-byte alignment
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 + 1024;
+
+template <int BN, int KB, int STAGES>
+struct TcCfg {
+    static_assert(BN == 128 || BN == 256, "BN");
+    static_assert(KB == 32 || KB == 64, "KB");
+    static constexpr int A_BYTES = TC_BM * KB * 2;          // one 128-row operand tile
+    static constexpr int B_BYTES = BN * KB * 2;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // Ah, Al, Bh, Bl
+    static constexpr int TMEM_COLS = 2 * BN;                 // two accumulators
+    static constexpr int EPI_FLOATS = 32 * 32;               // per epilogue warp
+    // barriers: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], done
+    static constexpr int NBARS = 2 * STAGES + 5;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + TC_EPI_WARPS * EPI_FLOATS * 4 +
+                                   NBARS * 8 + 64 + 1024;    // + 1024-byte alignment
+    // smem descriptor: layout type (2 = 128-byte swizzle, 4 = 64-byte) and
+    // the byte distance between 8-row groups
+    static constexpr unsigned long long SWZ = KB == 64 ? 2ull : 4ull;
+    static constexpr unsigned SBO = 8 * KB * 2;
+    // instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = BN
+    static constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                      ((unsigned)(BN >> 3) << 17) |
+                                      ((unsigned)(TC_BM >> 4) << 24);
+};
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -58,6 +84,10 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
     unsigned ok;
     asm volatile(
@@ -69,12 +99,13 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait for an mbarrier phase; false on timeout.
-__device__ bool mbar_wait(unsigned bar, unsigned parity) {
+// Bounded wait for an mbarrier phase; false on timeout or once another role
+// has raised the failure flag (fail may be null).
+__device__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int* fail) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try(bar, parity)) {
-        if (global_ns() - t0 > TC_WAIT_NS) return false;
+        if ((fail && *fail) || global_ns() - t0 > TC_WAIT_NS) return false;
     }
     return true;
 }
@@ -88,32 +119,27 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart (stage buffers are 1024-aligned).
+// Shared-memory matrix descriptor of a K-major swizzled operand whose rows
+// are KB*2 bytes and whose 8-row groups are SBO bytes apart (buffers are
+// 1024-byte aligned, so the swizzle phase starts at zero).
+template <class C>
 __device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
     unsigned long long d = 0;
     d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);        // start address
     d |= (unsigned long long)1 << 16;                           // leading byte offset (unused)
-    d |= (unsigned long long)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (unsigned long long)(C::SBO >> 4) << 32;               // stride byte offset
     d |= (unsigned long long)1 << 46;                           // descriptor version
-    d |= (unsigned long long)2 << 61;                           // 128-byte swizzle
+    d |= C::SWZ << 61;                                          // swizzle mode
     return d;
 }
 
-// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major,
-// M = 128, N = 128.
-constexpr unsigned kIdesc = (1u << 4)                  // D format F32
-                            | (1u << 7)                // A format BF16
-                            | (1u << 10)               // B format BF16
-                            | ((unsigned)(TC_TILE >> 3) << 17)   // N >> 3
-                            | ((unsigned)(TC_TILE >> 4) << 24);  // M >> 4
-
+template <class C>
 __device__ __forceinline__ void mma_bf16(unsigned tmem_d, unsigned long long a,
                                          unsigned long long b, unsigned accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+        "l"(a), "l"(b), "r"(C::IDESC), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(unsigned bar) {
@@ -122,18 +148,22 @@ __device__ __forceinline__ void mma_commit(unsigned bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
-    unsigned r[16];
+// 32 consecutive accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+    unsigned r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Centre (optional), split into bf16 hi/lo and transpose to [p][n_pad].
@@ -167,32 +197,65 @@ __global__ void tc_mean_kernel(const float* __restrict__ X, int n, int p, int ld
                         gridDim.x * blockDim.x);
 }
 
+// Tiles of 128 rows x BN columns holding an entry with column >= row:
+// row block tm keeps column blocks tn >= (128 tm) / BN.  Tiles are numbered
+// row block by row block.
+struct TileGrid {
+    int tm_count, tn_count, bn;
+    __host__ __device__ int first_tn(int tm) const { return (TC_BM * tm) / bn; }
+    __host__ __device__ int count() const {
+        int c = 0;
+        for (int tm = 0; tm < tm_count; ++tm) c += tn_count - first_tn(tm);
+        return c;
+    }
+    __device__ void coords(int idx, int& tm, int& tn) const {
+        int r = 0;
+        for (; r < tm_count - 1; ++r) {
+            const int c = tn_count - first_tn(r);
+            if (idx < c) break;
+            idx -= c;
+        }
+        tm = r;
+        tn = first_tn(r) + idx;
+    }
+};
+
+template <int BN, int KB, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap map_h,
                    const __grid_constant__ CUtensorMap map_l, int p, int n_pad, float inv_n,
-                   float* __restrict__ S, int lds) {
+                   float* __restrict__ S, int lds, TileGrid grid_tiles, int n_tiles) {
+    using C = TcCfg<BN, KB, STAGES>;
     extern __shared__ unsigned char smem_dyn[];
     // 1024-byte alignment for the swizzled operand tiles
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
     unsigned char* stages = smem;
-    unsigned long long* bars =
-        reinterpret_cast<unsigned long long*>(smem + TC_STAGES * TC_STAGE_BYTES);
-    // bars[0..S): full, bars[S..2S): empty, bars[2S]: done
-    volatile unsigned* tmem_slot = reinterpret_cast<volatile unsigned*>(bars + 2 * TC_STAGES + 1);
+    float* epi = reinterpret_cast<float*>(smem + (size_t)STAGES * C::STAGE_BYTES);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(epi + TC_EPI_WARPS * C::EPI_FLOATS);
+    unsigned long long* full = bars;
+    unsigned long long* empty = bars + STAGES;
+    unsigned long long* acc_full = bars + 2 * STAGES;
+    unsigned long long* acc_empty = bars + 2 * STAGES + 2;
+    unsigned long long* done = bars + 2 * STAGES + 4;
+    volatile unsigned* tmem_slot = reinterpret_cast<volatile unsigned*>(bars + C::NBARS);
     volatile int* fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* issued_slot = fail + 1;       // K blocks whose loads were issued
     volatile int* consumed_slot = fail + 2;     // K blocks whose loads the MMA issuer saw land
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = (p + TC_TILE - 1) / TC_TILE;
-    int tm, tn;
-    upper_tile(blockIdx.x, t, tm, tn);
-    const int m0 = tm * TC_TILE, n0 = tn * TC_TILE;
-    const int KT = n_pad / TC_KB;
+    const int KT = n_pad / KB;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * TC_STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), TC_EPI_WARPS);   // one arrival per epilogue warp
+        }
+        mbar_init(smem_u32(done), 1);
         *fail = 0;
         *issued_slot = 0;
         *consumed_slot = 0;
@@ -200,10 +263,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_h)));
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_l)));
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(const_cast<unsigned*>(tmem_slot))),
-                     "r"(TC_TMEM_COLS));
+                     "r"(C::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -211,102 +274,173 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // producer
-        for (int kt = 0; kt < KT && !*fail; ++kt) {
-            const int s = kt % TC_STAGES;
-            if (kt >= TC_STAGES &&
-                !mbar_wait(smem_u32(&bars[TC_STAGES + s]), ((kt / TC_STAGES) - 1) & 1)) {
-                *fail = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            int kb = 0;      // K blocks issued by this CTA over all its tiles
+            for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x) {
+                int tm, tn;
+                grid_tiles.coords(tile, tm, tn);
+                const int m0 = tm * TC_BM, n0 = tn * BN;
+                for (int kt = 0; kt < KT; ++kt, ++kb) {
+                    const int s = kb % STAGES;
+                    if (kb >= STAGES &&
+                        !mbar_wait(smem_u32(&empty[s]), ((kb / STAGES) - 1) & 1, fail)) {
+                        *fail = 1;
+                        break;
+                    }
+                    const unsigned fb = smem_u32(&full[s]);
+                    unsigned char* st = stages + (size_t)s * C::STAGE_BYTES;
+                    mbar_expect_tx(fb, C::STAGE_BYTES);
+                    const int x = kt * KB;
+                    tma_load_2d(smem_u32(st), &map_h, x, m0, fb);
+                    tma_load_2d(smem_u32(st + C::A_BYTES), &map_l, x, m0, fb);
+                    unsigned char* bh = st + 2 * C::A_BYTES;
+                    unsigned char* bl = bh + C::B_BYTES;
+#pragma unroll
+                    for (int h = 0; h < BN / TC_BM; ++h) {
+                        tma_load_2d(smem_u32(bh + h * C::A_BYTES), &map_h, x, n0 + h * TC_BM, fb);
+                        tma_load_2d(smem_u32(bl + h * C::A_BYTES), &map_l, x, n0 + h * TC_BM, fb);
+                    }
+                    *issued_slot = kb + 1;
+                }
             }
-            const unsigned full = smem_u32(&bars[s]);
-            unsigned char* st = stages + (size_t)s * TC_STAGE_BYTES;
-            mbar_expect_tx(full, TC_STAGE_BYTES);
-            const int x = kt * TC_KB;
-            tma_load_2d(smem_u32(st), &map_h, x, m0, full);
-            tma_load_2d(smem_u32(st + TC_OP_BYTES), &map_l, x, m0, full);
-            tma_load_2d(smem_u32(st + 2 * TC_OP_BYTES), &map_h, x, n0, full);
-            tma_load_2d(smem_u32(st + 3 * TC_OP_BYTES), &map_l, x, n0, full);
-            *issued_slot = kt + 1;
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        unsigned acc = 0;
-        int kt = 0;
-        for (; kt < KT; ++kt) {
-            const int s = kt % TC_STAGES;
-            if (!mbar_wait(smem_u32(&bars[s]), (kt / TC_STAGES) & 1)) {
-                *fail = 1;
-                break;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            int kb = 0, local = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++local) {
+                const int b = local & 1, u = local >> 1;
+                if (u >= 1 && !mbar_wait(smem_u32(&acc_empty[b]), (u - 1) & 1, fail)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned d = tmem + (unsigned)(b * BN);
+                for (int kt = 0; kt < KT; ++kt, ++kb) {
+                    const int s = kb % STAGES;
+                    if (!mbar_wait(smem_u32(&full[s]), (kb / STAGES) & 1, fail)) {
+                        ok = false;
+                        break;
+                    }
+                    *consumed_slot = kb + 1;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned base = smem_u32(stages + (size_t)s * C::STAGE_BYTES);
+                    const unsigned long long ah = smem_desc<C>(base),
+                                             al = smem_desc<C>(base + C::A_BYTES);
+                    const unsigned long long bh = smem_desc<C>(base + 2 * C::A_BYTES),
+                                             bl = smem_desc<C>(base + 2 * C::A_BYTES + C::B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < KB / 16; ++kk) {
+                        // advance 16 bf16 = 32 bytes along K inside the swizzled rows
+                        const unsigned long long off = (unsigned long long)((32 * kk) >> 4);
+                        mma_bf16<C>(d, ah + off, bh + off, (kt | kk) ? 1u : 0u);
+                        mma_bf16<C>(d, ah + off, bl + off, 1u);
+                        mma_bf16<C>(d, al + off, bh + off, 1u);
+                    }
+                    mma_commit(smem_u32(&empty[s]));       // stage s free when these finish
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&acc_full[b]));        // accumulator b ready
             }
-            *consumed_slot = kt + 1;
+            if (!ok) *fail = 1;
+            // every MMA issued above has finished once this commit arrives
+            mma_commit(smem_u32(done));
+            mbar_wait(smem_u32(done), 0, nullptr);
+        }
+    } else {
+        // epilogue: 8 warps; warp w reads accumulator lanes 32 (w % 4) .. +31,
+        // warps 2-5 the first half of the columns and warps 6-9 the second
+        const int ew = warp - TC_EPI_WARP0;
+        const int q = warp & 3, half = ew >> 2;
+        // 32 x 32 floats, row j at 32 j, its 16-byte groups XOR-swizzled by j
+        float4* buf = reinterpret_cast<float4*>(epi + ew * C::EPI_FLOATS);
+        const bool vec = (lds & 3) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
+        bool ok = true;
+        int local = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++local) {
+            int tm, tn;
+            grid_tiles.coords(tile, tm, tn);
+            const int m0 = tm * TC_BM + 32 * q, n0 = tn * BN;
+            const int b = local & 1, u = local >> 1;
+            if (ok) {
+                int got = 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&acc_full[b]), u & 1, fail) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, got, 0) != 0;
+                if (!ok && lane == 0) *fail = 1;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned base = smem_u32(stages + (size_t)s * TC_STAGE_BYTES);
-            const unsigned long long ah = smem_desc(base), al = smem_desc(base + TC_OP_BYTES);
-            const unsigned long long bh = smem_desc(base + 2 * TC_OP_BYTES),
-                                     bl = smem_desc(base + 3 * TC_OP_BYTES);
+            const int row = m0 + lane;
+            for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+                const int c0 = n0 + c;
+                // chunk outside S or wholly below the diagonal
+                if (m0 >= p || c0 >= p || c0 + 31 < m0) continue;
+                float v[32];
+                if (ok) {
+                    tmem_ld32(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(b * BN + c), v);
 #pragma unroll
-            for (int kk = 0; kk < TC_KB / 16; ++kk) {
-                // advance 16 bf16 = 32 bytes along K inside the swizzled rows
-                const unsigned long long off = (unsigned long long)((32 * kk) >> 4);
-                mma_bf16(tmem, ah + off, bh + off, acc);
-                acc = 1;
-                mma_bf16(tmem, ah + off, bl + off, 1);
-                mma_bf16(tmem, al + off, bh + off, 1);
+                    for (int i = 0; i < 32; ++i) v[i] *= inv_n;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = __int_as_float(0x7fc00000);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    buf[lane * 8 + (k ^ (lane & 7))] =
+                        make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                __syncwarp();
+                if (vec && c0 > m0 + 31 && c0 + 32 <= p && m0 + 32 <= p) {
+                    // interior chunk, strictly above the diagonal: no predicates
+                    float* dm = S + (size_t)c0 * lds + row;       // mirror S_kj, lanes along row k
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) dm[(size_t)i * lds] = v[i];
+                    const int g = lane & 7;                       // S_jk, 4 rows x 128 bytes per store
+#pragma unroll
+                    for (int jj = 0; jj < 32; jj += 4) {
+                        const int j = jj + (lane >> 3);
+                        *reinterpret_cast<float4*>(S + (size_t)(m0 + j) * lds + c0 + 4 * g) =
+                            buf[j * 8 + (g ^ (j & 7))];
+                    }
+                } else {
+                    // diagonal or ragged chunk: S_kj for k > j, S_jk for k >= j
+                    if (row < p) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int col = c0 + i;
+                            if (col < p && col > row) S[(size_t)col * lds + row] = v[i];
+                        }
+                    }
+                    const int col = c0 + lane;
+                    const float* bf = reinterpret_cast<const float*>(buf);
+#pragma unroll 8
+                    for (int j = 0; j < 32; ++j) {
+                        const int r = m0 + j;
+                        if (r < p && col < p && col >= r)
+                            S[(size_t)r * lds + col] = bf[(j * 8 + ((lane >> 2) ^ (j & 7))) * 4 + (lane & 3)];
+                    }
+                }
+                __syncwarp();
             }
-            mma_commit(smem_u32(&bars[TC_STAGES + s]));   // stage s free when these finish
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
         }
-        mma_commit(smem_u32(&bars[2 * TC_STAGES]));       // accumulator ready
     }
-    __syncwarp();
-
-    // epilogue: wait for the accumulator (bounded)
-    if (!mbar_wait(smem_u32(&bars[2 * TC_STAGES]), 0)) *fail = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
-    const bool good = (*fail == 0);                          // same value in every thread
-    if (!good && threadIdx.x == 0) {
-        // let copies still in flight land before the stages are reused (bounded)
+    if (*fail && threadIdx.x == 0) {
+        // let copies still in flight land before the CTA exits (bounded)
         const int issued = *issued_slot, consumed = *consumed_slot;
-        for (int kt = consumed; kt < issued; ++kt)
-            mbar_wait(smem_u32(&bars[kt % TC_STAGES]), (kt / TC_STAGES) & 1);
-    }
-    __syncthreads();
-    float* stage_out = reinterpret_cast<float*>(stages);      // 128 x 129 floats, reuses stages
-    const int row = warp * 32 + lane;
-    for (int c = 0; c < TC_TILE; c += 16) {
-        float v[16];
-        if (good) {
-            tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c, v);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = __int_as_float(0x7fc00000);
-        }
-#pragma unroll
-        for (int i = 0; i < 16; ++i) stage_out[row * (TC_TILE + 1) + c + i] = good ? v[i] * inv_n : v[i];
+        for (int kb = consumed; kb < issued; ++kb)
+            mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1, nullptr);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    for (int e = threadIdx.x; e < TC_TILE * TC_TILE; e += TC_THREADS) {
-        const int r = e / TC_TILE, c = e % TC_TILE;
-        // on a diagonal tile (j, k) and (k, j) come out of different accumulation
-        // orders; store the upper triangle's value in both so S is exactly symmetric
-        const int rr = (tm == tn && c < r) ? c : r, cc = (tm == tn && c < r) ? r : c;
-        if (m0 + r < p && n0 + c < p)
-            S[(size_t)(m0 + r) * lds + n0 + c] = stage_out[rr * (TC_TILE + 1) + cc];
-    }
-    if (tm != tn) {
-        for (int e = threadIdx.x; e < TC_TILE * TC_TILE; e += TC_THREADS) {
-            const int r = e / TC_TILE, c = e % TC_TILE;     // mirror row r = col of the tile
-            if (n0 + r < p && m0 + c < p)
-                S[(size_t)(n0 + r) * lds + m0 + c] = stage_out[c * (TC_TILE + 1) + r];
-        }
-    }
-    __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TC_TMEM_COLS));
+                     "r"(C::TMEM_COLS));
     }
 }
 
@@ -329,7 +463,47 @@ EncodeTiled encoder() {
     return fn;
 }
 
-int pad_n(int n) { return (n + TC_KB - 1) / TC_KB * TC_KB; }
+constexpr int TC_NPAD = 64;
+int pad_n(int n) { return (n + TC_NPAD - 1) / TC_NPAD * TC_NPAD; }
+
+// Operand maps over XhT / XlT ([p][n_pad] bf16): boxes of KB x 128 rows.
+template <int KB>
+bool encode_maps(EncodeTiled enc, CUtensorMap& mh, CUtensorMap& ml, void* XhT, void* XlT, int p,
+                 int n_pad) {
+    const cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)p};
+    const cuuint64_t strides[1] = {(cuuint64_t)n_pad * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)KB, (cuuint32_t)TC_BM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle swz = KB == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    return enc(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XhT, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+           enc(&ml, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XlT, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int KB, int STAGES>
+cudaError_t launch_tiles(EncodeTiled enc, void* XhT, void* XlT, int n, int p, int n_pad, float* S,
+                         int lds, cudaStream_t st) {
+    using C = TcCfg<BN, KB, STAGES>;
+    CUtensorMap mh, ml;
+    if (!encode_maps<KB>(enc, mh, ml, XhT, XlT, p, n_pad)) return cudaErrorInvalidValue;
+    auto kern = gram_tc_kernel<BN, KB, STAGES>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    TileGrid g{(p + TC_BM - 1) / TC_BM, (p + BN - 1) / BN, BN};
+    const int n_tiles = g.count();
+    const int grid = n_tiles < sms ? n_tiles : sms;
+    kern<<<grid, TC_THREADS, C::SMEM, st>>>(mh, ml, p, n_pad, (float)(1.0 / (double)n), S, lds, g,
+                                            n_tiles);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -351,27 +525,13 @@ cudaError_t launch_gram_tc(const float* X, int n, int p, int ldx, int center, fl
     if (center) tc_mean_kernel<<<(p + 255) / 256, 256, 0, st>>>(X, n, p, ldx, mu);
     split_transpose_kernel<<<dim3(n_pad / 32, (p + 31) / 32), dim3(32, 8), 0, st>>>(
         X, n, p, ldx, center ? mu : nullptr, XhT, XlT, n_pad);
-
-    CUtensorMap mh, ml;
-    const cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)p};
-    const cuuint64_t strides[1] = {(cuuint64_t)n_pad * 2};
-    const cuuint32_t box[2] = {TC_KB, TC_TILE};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XhT, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
-    if (enc(&ml, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XlT, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TC_SMEM);
-    if (e != cudaSuccess) return e;
-    const int t = (p + TC_TILE - 1) / TC_TILE;
-    gram_tc_kernel<<<t * (t + 1) / 2, TC_THREADS, TC_SMEM, st>>>(mh, ml, p, n_pad,
-                                                                 (float)(1.0 / (double)n), S, lds);
-    return cudaGetLastError();
+    // 128 x 256 tiles cut the operand traffic per flop by a quarter against
+    // 128 x 128 and keep the MMA operand reads within shared-memory
+    // bandwidth; two 96 KB stages of 128-byte-swizzled K blocks of 64 ran
+    // faster than four 48 KB stages of 64-byte-swizzled blocks of 32.  Small
+    // p keeps 128-column tiles for more tiles per SM.
+    if (p > 1024) return launch_tiles<256, 64, 2>(enc, XhT, XlT, n, p, n_pad, S, lds, st);
+    return launch_tiles<128, 64, 3>(enc, XhT, XlT, n, p, n_pad, S, lds, st);
 }
 
 }  // namespace spmesl

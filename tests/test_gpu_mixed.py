@@ -21,7 +21,10 @@ import paper_2203_15031_gb300 as sp  # noqa: E402
 DEV = torch.device("cuda", 0)
 
 
-@pytest.mark.parametrize("n,p", [(75, 130), (1, 3), (64, 128), (200, 300), (500, 257), (129, 1000)])
+# p <= 1024 runs 128 x 128 tiles; larger p 128 x 256 tiles, and at p = 4000
+# (272 tiles) CTAs loop over several tiles through both accumulators
+@pytest.mark.parametrize("n,p", [(75, 130), (1, 3), (64, 128), (200, 300), (500, 257), (129, 1000),
+                                 (100, 1300), (33, 2333), (70, 4000)])
 @pytest.mark.parametrize("center", [False, True])
 def test_split_bf16_gram_matches_fp64(n, p, center):
     rng = np.random.default_rng(n + 7 * p)
