@@ -172,8 +172,11 @@ __global__ void __launch_bounds__(512) batch_cd_kernel(const BatchFit* __restric
 }
 
 // Lazy gradient over all columns of all fits; overflowing columns are queued.
+// At most 8 warps a block and 3 blocks an SM: the kernel then keeps its
+// working set in registers (79) instead of spilling inside the sweep.
+constexpr int LAZY_MAX_WARPS = 8;
 template <typename T, bool STD>
-__global__ void __launch_bounds__(512) batch_cd_lazy_kernel(const BatchFit* __restrict__ fits,
+__global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(const BatchFit* __restrict__ fits,
                                                             const int* __restrict__ col_prefix,
                                                             int count, int total_cols, int max_ldp,
                                                             double tol, int maxit,
@@ -322,7 +325,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     if (lazy) {
         // W (tuned) shapes the lazy launch, which does almost all the work
         const size_t lper = lazy_warp_smem_bytes<T>(b->max_ldp);
-        const int LW = std::max(1, std::min({W, 16, (int)(budget / lper)}));
+        const int LW = std::max(1, std::min({W, LAZY_MAX_WARPS, (int)(budget / lper)}));
         const size_t lsm = lper * LW;
         auto lk = b->standardize ? batch_cd_lazy_kernel<T, true> : batch_cd_lazy_kernel<T, false>;
         if ((e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -640,6 +643,8 @@ spmesl_status spmesl_batch_tune(spmesl_batch* b, void* workspace, size_t ws_byte
     float best = 1e30f;
     int bestW = auto_warps(b);
     for (int W : cand) {
+        // with the lazy gradient W shapes only the lazy launch, capped at LAZY_MAX_WARPS
+        if (b->gradient != SPMESL_GRADIENT_EAGER && W > LAZY_MAX_WARPS) continue;
         b->warps_per_block = W;
         float tot = 0.f;
         bool ok = true;

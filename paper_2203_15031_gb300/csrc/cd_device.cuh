@@ -516,6 +516,21 @@ __device__ __forceinline__ void load4g(const T* __restrict__ src, T (&v)[4]) {
     }
 }
 
+// Chunks of [from, from + 32) that the sweep must scan, as a bit mask: with
+// the standardised matrix, a chunk is skipped when chunk_skippable proves
+// that none of its coordinates can move; the test reads only the chunk's
+// summary and the column's running sums, so the lanes test 32 chunks at once.
+// The mask stays valid until a move changes the running sums.
+template <bool STD>
+__device__ __forceinline__ unsigned chunks_to_scan(const ColScan& cs, int from, int nch, float lam) {
+    const int ci = from + (int)(threadIdx.x & 31);
+    bool need = ci < nch;
+    if constexpr (STD) {
+        if (need) need = !chunk_skippable(cs.ci[ci], cs, lam);
+    }
+    return __ballot_sync(FULL_MASK, need);
+}
+
 // One sweep; returns max |delta b|.  Sets `overflow` and stops early if the
 // support list is full.
 template <typename T, bool STD>
@@ -525,15 +540,24 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
     const int p = a.p;
     const int ldp = a.ldp;
     const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
+    const int nch = (p + CHUNK - 1) / CHUNK;
     T maxd = T(0);
     int e0 = 0;                                   // first support entry with idx >= cb
-    for (int cb = 0, ci = 0; cb < p; cb += CHUNK, ++ci) {
+    int mbase = 0;
+    unsigned mask = chunks_to_scan<STD>(cs, 0, nch, (float)lam);
+    for (;;) {
+        if (mask == 0u) {
+            mbase += 32;
+            if (mbase >= nch) break;
+            mask = chunks_to_scan<STD>(cs, mbase, nch, (float)lam);
+            continue;
+        }
+        const int ci = mbase + __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const int cb = ci * CHUNK;
         while (e0 < s.n && s.idx[e0] < cb) ++e0;
         int e1 = e0;
         while (e1 < s.n && s.idx[e1] < cb + CHUNK) ++e1;
-        if constexpr (STD) {
-            if (e1 == e0 && chunk_skippable(cs.ci[ci], cs, (float)lam)) continue;
-        }
         const int k0 = cb + lane * SCAN_V;
         const bool in = k0 < ldp;                 // the whole quad is inside the padded row
         // slice of g: S_jk - sum_{l in support} S_lk b_l
@@ -560,6 +584,7 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
                     if (u == t) bv[u] = s.val[e];
             }
         }
+        const unsigned nmoves0 = cs.nmoves;
         int cursor = cb;
         for (;;) {
             T nbv[SCAN_V];
@@ -628,6 +653,14 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
             if (lane == 0) cs.ci[ci] = ChunkInfo{mx, cs.dsum, cs.nmoves, e1 - e0};
+            __syncwarp();
+            // moves raised the running sums: test the chunks after this one again
+            if (cs.nmoves != nmoves0) {
+                mbase = ci + 1;
+                if (mbase >= nch) break;
+                mask = chunks_to_scan<STD>(cs, mbase, nch, (float)lam);
+            }
+        } else {
             __syncwarp();
         }
     }
