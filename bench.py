@@ -41,7 +41,12 @@ if ROOT not in sys.path:
 METRIC = "SPMESL solves/s + p99 latency, mixed-prec batched vs plain GPU @ dTheta<=1e-4"
 WORKLOAD = "er_p2000_n200_fp32"
 N_DATASETS = 10
-KERNELS_PER_SOLVE = 6        # per batched step: gram, prep_diag, prep_matrix, lazy cd, eager cd queue, theta
+# the headline batched path: split-BF16 Gram on the tensor cores, CD in FP32,
+# sigma / convergence / Theta in FP64
+BATCH_PREC = "mixed"
+# per batched step: split/transpose, tcgen05 Gram, prep_diag, prep_matrix, lazy
+# cd, eager cd queue, theta (the FP32 path has one SIMT Gram launch instead of two)
+KERNELS_PER_SOLVE = {"mixed": 7, "fp32": 6}
 
 
 def _env_rank():
@@ -121,9 +126,11 @@ def make_inputs(count: int):
     return w, probs
 
 
-def cpu_baseline(w, prob, budget_s: float = 20.0):
+def cpu_baseline(w, prob, budget_s: float = 20.0, theta_gpu=None):
     """FP64 oracle (as it stands) on the host cores: one whole solve (Gram +
-    Algorithm 2) of dataset seed 0, repeated while it stays inside the budget."""
+    Algorithm 2) of dataset seed 0, repeated while it stays inside the budget.
+    With theta_gpu (the GPU's Theta of the same dataset) it also returns
+    max|dTheta| / max|Theta| of that result against the oracle's."""
     import numpy as np
     import oracle
     oracle.build()
@@ -134,14 +141,18 @@ def cpu_baseline(w, prob, budget_s: float = 20.0):
     while True:
         t0 = time.perf_counter()
         S = oracle.gram(X64)
-        oracle.spmesl(S, prob.lambda0, tol=w["tol"], maxit=w["maxit"], nthreads=cores)
+        ref = oracle.spmesl(S, prob.lambda0, tol=w["tol"], maxit=w["maxit"], nthreads=cores)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start > budget_s or len(times) >= 5:
             break
     t = statistics.median(times)
-    return {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(times)} whole solves (FP64 Gram + Algorithm 2, OpenMP over columns) "
-                      f"of the ER p={prob.p} n={prob.n} dataset seed 0, median {t:.3f} s"}
+    out = {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(times)} whole solves (FP64 Gram + Algorithm 2, OpenMP over columns) "
+                     f"of the ER p={prob.p} n={prob.n} dataset seed 0, median {t:.3f} s"}
+    if theta_gpu is not None:
+        T = ref["Theta"]
+        out["gpu_max_rel_dtheta"] = float(np.max(np.abs(theta_gpu - T)) / np.max(np.abs(T)))
+    return out
 
 
 def run_reference(args):
@@ -212,25 +223,26 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
-    # ---- batched path (headline): one batch = the ten datasets
-    bt = sp.Batch(inputs, kind="X", precision="fp32", tol=tol, maxit=maxit,
-                  record_phase_times=True)
-    bt.run()
-    bt.result()
-    best_w = bt.tune()
-    for _ in range(args.warmup):
+    # ---- batched paths: one batch = the ten datasets
+    def batched(prec, sampler=None):
+        bt = sp.Batch(inputs, kind="X", precision=prec, tol=tol, maxit=maxit,
+                      record_phase_times=True)
         bt.run()
-    statuses, _ = bt.result()
-    if any(s != sp.SPMESL_OK for s in statuses):
-        raise RuntimeError(f"warm-up fits did not converge: {statuses}")
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    cd_ms, moves = [], []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
+        bt.result()
+        best_w = bt.tune()
+        for _ in range(args.warmup):
+            bt.run()
+        statuses, _ = bt.result()
+        if any(s != sp.SPMESL_OK for s in statuses):
+            raise RuntimeError(f"warm-up fits did not converge: {statuses}")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        cd_ms, moves = [], []
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__enter__()
         for i in range(args.steps):
             flush.zero_()                   # evict the inputs from L2 between steps
             ev[i][0].record(stream)
@@ -240,15 +252,24 @@ def run_ours(args):
             cd_ms.append(st["ms_cd"])
             moves.append(st["moves"])
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    per = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(per)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        if sampler:
+            sampler.__exit__(None, None, None)
+        if world > 1:
+            dist.barrier()
+        per = [a.elapsed_time(b) for a, b in ev]
+        total_ms = sum(per)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return bt, best_w, per, total_ms, cd_ms, moves
+
+    clk = ClockSampler(local_rank)
+    bt, best_w, per, total_ms, cd_ms, moves = batched(BATCH_PREC, clk)       # headline
     value = world * N_DATASETS * args.steps / (total_ms / 1e3)
+    bt32, _, per32, total32, _, _ = batched("fp32")
+    value32 = world * N_DATASETS * args.steps / (total32 / 1e3)
+    bt32.close()
 
     # ---- plain path: one fit per launch sequence, serialised on one stream
     S = torch.empty((p, p), dtype=torch.float32, device=dev)
@@ -282,6 +303,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_per = [a.elapsed_time(b) for a, b in pev]
     plain_value = len(plain_per) / (sum(plain_per) / 1e3)
+    plain_fit(0)                            # dataset 0 against the batched result
+    torch.cuda.synchronize()
+    dtheta_plain = float((bt.Theta[0] - Theta).abs().max() / Theta.abs().max())
 
     # ---- end to end through the public API with host buffers (pinned)
     Xh = [torch.from_numpy(pr.X).pin_memory() for pr in probs]
@@ -338,7 +362,12 @@ def run_ours(args):
         lat = {"batched_p50_ms": statistics.median(per), "batched_p99_ms": q99(srt),
                "plain_p50_ms": statistics.median(plain_per), "plain_p99_ms": q99(psrt),
                "unit": "ms from launch to completion of a solve (device)"}
-        cb = cpu_baseline(w, probs[0]) if world == 1 and not args.no_cpu_baseline else None
+        cb = (cpu_baseline(w, probs[0], theta_gpu=bt.Theta[0].cpu().numpy())
+              if world == 1 and not args.no_cpu_baseline else None)
+        acc = {"max_rel_dtheta_vs_plain_fp32": dtheta_plain, "dataset": "seed 0",
+               "bound": 1e-4}
+        if cb is not None:
+            acc["max_rel_dtheta_vs_fp64_oracle"] = cb.pop("gpu_max_rel_dtheta")
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -346,14 +375,20 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "p": p, "n": n, "network": "erdos_renyi",
                            "fits_per_step": N_DATASETS, "seeds": "0-9",
                            "lambda0": "sqrt(2 log p / n)", "tol": tol, "maxit": maxit,
-                           "gram": "fp32", "cd": "fp32", "sigma_theta": "fp64",
+                           "precision": BATCH_PREC,
+                           "gram": "split-bf16 on tcgen05 (hi*hi + hi*lo + lo*hi, fp32 accumulation)",
+                           "cd": "fp32", "sigma_theta": "fp64",
                            "inner_rule": "column", "path": "batched (one launch per phase)",
                            "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}"},
-                "plain": {"value": plain_value, "unit": "solves/s",
+                "plain": {"value": plain_value, "unit": "solves/s", "precision": "fp32",
                           "path": "one spmesl_gram + spmesl_fit per fit, serialised"},
+                "batched_fp32": {"value": value32, "unit": "solves/s",
+                                 "p50_ms": statistics.median(per32),
+                                 "path": "the same batch with the FP32 SIMT Gram"},
+                "accuracy": acc,
                 "latency": lat, "e2e": e2e, "roofline": roof, "cpu_baseline": cb,
-                "gpu_launches": KERNELS_PER_SOLVE * args.steps,
+                "gpu_launches": KERNELS_PER_SOLVE[BATCH_PREC] * args.steps,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     bt.close()

@@ -1,5 +1,9 @@
 // Batched SPMESL: many independent fits of different p and n in one pass of
 // four launches (Gram tiles, standardisation, coordinate descent, Theta).
+// With SPMESL_MIXED the Gram of every fit given as X runs as split-BF16
+// products on the tensor cores (one batched split/transpose launch, then one
+// persistent tcgen05 launch over the tiles of all fits); the rest runs in
+// FP32 with sigma and Theta in FP64, as in the single-fit path.
 //
 // Every launch covers all fits at once.  Fits are ordered by decreasing p so
 // the longest column chains start first.  A descriptor table in the
@@ -11,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -18,6 +23,7 @@
 
 #include "cd_device.cuh"
 #include "gram_device.cuh"
+#include "gram_tc.cuh"
 
 namespace spmesl {
 
@@ -36,10 +42,13 @@ struct BatchFit {
     double* Theta;
     double* sigma_out;
     FitCtrl* ctrl;
+    void* XhT;            // split-BF16 operands (SPMESL_MIXED with X)
+    void* XlT;
     double lambda0;
     int n, p, ldp;
     int col_start, gram_start, theta_start;
-    int pad[2];
+    int split_start;      // first block of the batched split/transpose launch
+    int pad;
 };
 
 thread_local bool g_batch_pageable_staging = false;
@@ -81,6 +90,20 @@ __global__ void __launch_bounds__(256) batch_gram_kernel(const BatchFit* __restr
     upper_tile(blockIdx.x - f.gram_start, t, tm, tn);
     gram_tile<T>(static_cast<const T*>(f.X), f.n, f.p, f.p, static_cast<const T*>(f.mu),
                  static_cast<T*>(f.Sg), f.p, (T)(1.0 / (double)f.n), tm, tn);
+}
+
+// Split/transpose of every fit given as X (SPMESL_MIXED): blocks of 32 x 32
+// over each fit's padded sample dimension and columns; blockDim 32 x 8.
+__global__ void batch_split_kernel(const BatchFit* __restrict__ fits,
+                                   const int* __restrict__ split_prefix, int count) {
+    const int fi = find_fit(split_prefix, count, blockIdx.x);
+    const BatchFit& f = fits[fi];
+    const int n_pad = tc_pad_n(f.n);
+    const int bx = n_pad / 32;
+    const int idx = blockIdx.x - f.split_start;
+    split_transpose_tile(static_cast<const float*>(f.X), f.n, f.p, f.p,
+                         static_cast<const float*>(f.mu), static_cast<__nv_bfloat16*>(f.XhT),
+                         static_cast<__nv_bfloat16*>(f.XlT), n_pad, (idx % bx) * 32, (idx / bx) * 32);
 }
 
 template <typename T>
@@ -228,7 +251,8 @@ struct FitPlan {
     double* Theta;
     double* sigma;
     size_t off_ctrl, off_cs, off_csf, off_sigma, off_status, off_diag, off_mu, off_Sg, off_SC, off_BT;
-    int col_start, gram_start, theta_start;
+    size_t off_XhT, off_XlT;
+    int col_start, gram_start, theta_start, split_start;
 };
 
 int num_sms() {
@@ -270,6 +294,9 @@ struct spmesl_batch {
     size_t off_ovf = 0;            // queue of columns for the eager launch (total_cols ints)
     std::vector<FitPlan> plan;     // ordered by decreasing p
     size_t off_hdr = 0, off_desc = 0, off_colp = 0, off_gramp = 0, off_thetap = 0, off_ctrls = 0;
+    // SPMESL_MIXED: tensor-core Gram table, fit of every tile, split prefixes
+    size_t off_tcfit = 0, off_tilefit = 0, off_splitp = 0;
+    int total_split = 0;
     size_t ws_bytes = 0;
     int total_cols = 0, total_gram = 0, total_theta = 0, max_ldp = 32, max_p = 2, max_n = 1;
     bool any_x = false;
@@ -309,7 +336,16 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     if (b->any_x) {
         if (b->center)
             batch_mean_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits);
-        batch_gram_kernel<T><<<b->total_gram, 256, 0, st>>>(fits, gramp, count);
+        if (b->precision == SPMESL_MIXED) {
+            batch_split_kernel<<<b->total_split, dim3(32, 8), 0, st>>>(
+                fits, reinterpret_cast<const int*>(ws + b->off_splitp), count);
+            if ((e = launch_gram_tc_batch(reinterpret_cast<const TcFit*>(ws + b->off_tcfit),
+                                          reinterpret_cast<const int*>(ws + b->off_tilefit),
+                                          b->total_gram, st)) != cudaSuccess)
+                return e;
+        } else {
+            batch_gram_kernel<T><<<b->total_gram, 256, 0, st>>>(fits, gramp, count);
+        }
     }
     batch_prep_diag_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits,
                                                                                    b->standardize);
@@ -377,8 +413,12 @@ int auto_warps(const spmesl_batch* b) {
 }
 
 // Fill the pinned table with device addresses inside `ws`.
-void stage_table(spmesl_batch* b, unsigned char* ws) {
+bool stage_table(spmesl_batch* b, unsigned char* ws) {
     BatchFit* t = reinterpret_cast<BatchFit*>(b->pinned);
+    const bool mixed = b->precision == SPMESL_MIXED;
+    TcFit* tcf = mixed ? reinterpret_cast<TcFit*>(b->pinned + (b->off_tcfit - b->off_desc)) : nullptr;
+    int* tilefit = mixed ? reinterpret_cast<int*>(b->pinned + (b->off_tilefit - b->off_desc)) : nullptr;
+    int* splitp = mixed ? reinterpret_cast<int*>(b->pinned + (b->off_splitp - b->off_desc)) : nullptr;
     int* colp = reinterpret_cast<int*>(b->pinned + (b->off_colp - b->off_desc));
     int* gramp = reinterpret_cast<int*>(b->pinned + (b->off_gramp - b->off_desc));
     int* thetap = reinterpret_cast<int*>(b->pinned + (b->off_thetap - b->off_desc));
@@ -396,6 +436,8 @@ void stage_table(spmesl_batch* b, unsigned char* ws) {
         d.csf = reinterpret_cast<float*>(ws + f.off_csf);
         d.sigma = reinterpret_cast<double*>(ws + f.off_sigma);
         d.col_status = reinterpret_cast<int*>(ws + f.off_status);
+        d.XhT = (mixed && f.X) ? ws + f.off_XhT : nullptr;
+        d.XlT = (mixed && f.X) ? ws + f.off_XlT : nullptr;
         d.Theta = f.Theta;
         d.sigma_out = f.sigma;
         d.ctrl = reinterpret_cast<FitCtrl*>(ws + f.off_ctrl);
@@ -406,7 +448,21 @@ void stage_table(spmesl_batch* b, unsigned char* ws) {
         d.col_start = f.col_start;
         d.gram_start = f.gram_start;
         d.theta_start = f.theta_start;
+        d.split_start = f.split_start;
         t[i] = d;
+        if (mixed) {
+            splitp[i] = f.split_start;
+            if (f.X) {
+                if (!tc_encode_fit(tcf[i], d.XhT, d.XlT, f.n, f.p, static_cast<float*>(d.Sg), f.p,
+                                   f.gram_start, TC_BATCH_BN))
+                    return false;
+                const int nt = tcf[i].g.count();
+                for (int k = 0; k < nt; ++k) tilefit[f.gram_start + k] = i;
+            } else {
+                tcf[i] = TcFit{};
+                tcf[i].tile_start = f.gram_start;
+            }
+        }
         colp[i] = f.col_start;
         gramp[i] = f.gram_start;
         thetap[i] = f.theta_start;
@@ -414,7 +470,9 @@ void stage_table(spmesl_batch* b, unsigned char* ws) {
     colp[b->count] = b->total_cols;
     gramp[b->count] = b->total_gram;
     thetap[b->count] = b->total_theta;
+    if (mixed) splitp[b->count] = b->total_split;
     b->table_ws = ws;
+    return true;
 }
 
 spmesl_status status_of(const FitCtrl& c) {
@@ -437,7 +495,8 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     if (opts) o = *opts;
     else spmesl_default_opts(&o);
     if (!probs || count < 1 || !(tol > 0.0) || maxit < 1) return SPMESL_EINVAL;
-    if (o.precision != SPMESL_FP64 && o.precision != SPMESL_FP32) return SPMESL_EINVAL;
+    if (o.precision != SPMESL_FP64 && o.precision != SPMESL_FP32 && o.precision != SPMESL_MIXED)
+        return SPMESL_EINVAL;
     if (o.inner_rule != SPMESL_INNER_COLUMN) return SPMESL_EINVAL;
     const int maxp = max_p_for(o.precision);
     for (int i = 0; i < count; ++i) {
@@ -465,15 +524,27 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int c) { return probs[a].p > probs[c].p; });
     const size_t s = (size_t)elem_size(o.precision);
+    const bool mixed = o.precision == SPMESL_MIXED;
+    // tensor-core tiles of the whole batch (SPMESL_MIXED), for the table sizes
+    long long tc_tiles = 0;
+    if (mixed)
+        for (int i = 0; i < count; ++i)
+            if (probs[i].X) tc_tiles += tc_tile_grid(probs[i].p, TC_BATCH_BN).count();
+    if (tc_tiles > (1ll << 30)) return SPMESL_EINVAL;
     size_t off = 0;
     b->off_hdr = off;   off += align_up(sizeof(BatchHeader), 256);
     b->off_desc = off;  off += align_up(sizeof(BatchFit) * count, 256);
     b->off_colp = off;  off += align_up(sizeof(int) * (count + 1), 256);
     b->off_gramp = off; off += align_up(sizeof(int) * (count + 1), 256);
     b->off_thetap = off; off += align_up(sizeof(int) * (count + 1), 256);
+    if (mixed) {
+        b->off_tcfit = off;   off += align_up(sizeof(TcFit) * count, 256);
+        b->off_tilefit = off; off += align_up(sizeof(int) * (size_t)std::max<long long>(tc_tiles, 1), 256);
+        b->off_splitp = off;  off += align_up(sizeof(int) * (count + 1), 256);
+    }
     b->table_bytes = off - b->off_desc;
     b->off_ctrls = off; off += (size_t)256 * count;      // one FitCtrl slot per fit
-    int cols = 0, gram = 0, theta = 0;
+    int cols = 0, gram = 0, theta = 0, split = 0;
     for (int k = 0; k < count; ++k) {
         const spmesl_problem& q = probs[order[k]];
         FitPlan f{};
@@ -496,6 +567,11 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
         if (q.X) {
             f.off_mu = off;  off += align_up((size_t)f.p * s, 256);
             f.off_Sg = off;  off += align_up((size_t)f.p * f.p * s, 256);
+            if (mixed) {
+                const size_t half = tc_operand_bytes(f.n, f.p) / 2;
+                f.off_XhT = off; off += half;
+                f.off_XlT = off; off += half;
+            }
             b->any_x = true;
         }
         f.off_SC = off;     off += mat;
@@ -503,7 +579,11 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
         f.col_start = cols;
         cols += f.p;
         f.gram_start = gram;
-        if (q.X) {
+        f.split_start = split;
+        if (q.X && mixed) {
+            gram += tc_tile_grid(f.p, TC_BATCH_BN).count();
+            split += (tc_pad_n(f.n) / 32) * ((f.p + 31) / 32);
+        } else if (q.X) {
             const int t = (f.p + GRAM_BM - 1) / GRAM_BM;
             gram += t * (t + 1) / 2;
         }
@@ -517,6 +597,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     }
     b->total_cols = cols;
     b->total_gram = gram;
+    b->total_split = split;
     b->total_theta = theta;
     b->off_ovf = off;
     off += align_up(sizeof(int) * (size_t)cols, 256);
@@ -524,7 +605,8 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     if (spmesl::g_batch_pageable_staging) {
         // used by the serving context: no pinned allocation (whose release can
         // synchronise the device) per admission round
-        b->pinned = static_cast<unsigned char*>(malloc(b->table_bytes));
+        // (256-byte aligned: the table holds 64-byte aligned tensor maps)
+        b->pinned = static_cast<unsigned char*>(std::aligned_alloc(256, align_up(b->table_bytes, 256)));
         b->pinned_is_pageable = true;
         if (!b->pinned) {
             delete b;
@@ -548,7 +630,10 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
     if (b->table_ws != workspace) {
         // the staged table may still be read by an earlier copy on `st`
         if (b->table_ws && cudaStreamSynchronize(st) != cudaSuccess) return SPMESL_ECUDA;
-        stage_table(b, ws);
+        if (!stage_table(b, ws)) {
+            b->table_ws = nullptr;
+            return SPMESL_ECUDA;
+        }
     }
     const int W = b->warps_per_block > 0 ? b->warps_per_block : auto_warps(b);
     auto enqueue = [&](cudaStream_t s2) {
@@ -680,7 +765,7 @@ void spmesl_batch_destroy(spmesl_batch* b) {
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
     if (b->ev[1]) cudaEventDestroy(b->ev[1]);
     if (b->pinned) {
-        if (b->pinned_is_pageable) free(b->pinned);
+        if (b->pinned_is_pageable) std::free(b->pinned);
         else cudaFreeHost(b->pinned);
     }
     delete b;

@@ -37,12 +37,12 @@
 #include <mutex>
 
 #include "gram_device.cuh"
+#include "gram_tc.cuh"
 
 namespace spmesl {
 
 namespace {
 
-constexpr int TC_BM = 128;            // accumulator rows = TMEM lanes
 constexpr int TC_THREADS = 320;       // producer, MMA, 8 epilogue warps
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_EPI_WARP0 = 2;
@@ -59,8 +59,9 @@ struct TcCfg {
     static constexpr int EPI_FLOATS = 32 * 32;               // per epilogue warp
     // barriers: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], done
     static constexpr int NBARS = 2 * STAGES + 5;
+    // + tensor-memory address, flags and the K-block ring, + 1024-byte alignment
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + TC_EPI_WARPS * EPI_FLOATS * 4 +
-                                   NBARS * 8 + 64 + 1024;    // + 1024-byte alignment
+                                   NBARS * 8 + 64 + 1024;
     // smem descriptor: layout type (2 = 128-byte swizzle, 4 = 64-byte) and
     // the byte distance between 8-row groups
     static constexpr unsigned long long SWZ = KB == 64 ? 2ull : 4ull;
@@ -170,26 +171,7 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
 __global__ void split_transpose_kernel(const float* __restrict__ X, int n, int p, int ldx,
                                        const float* __restrict__ mu, __nv_bfloat16* __restrict__ XhT,
                                        __nv_bfloat16* __restrict__ XlT, int n_pad) {
-    __shared__ float tile[32][33];
-    const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;            // 32 x 8
-    for (int r = ty; r < 32; r += 8) {
-        const int i = i0 + r, c = c0 + tx;
-        float v = 0.f;
-        if (i < n && c < p) v = X[(size_t)i * ldx + c] - (mu ? mu[c] : 0.f);
-        tile[r][tx] = v;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int c = c0 + r, i = i0 + tx;
-        if (c < p && i < n_pad) {
-            const float v = tile[tx][r];
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-            XhT[(size_t)c * n_pad + i] = h;
-            XlT[(size_t)c * n_pad + i] = l;
-        }
-    }
+    split_transpose_tile(X, n, p, ldx, mu, XhT, XlT, n_pad, blockIdx.x * 32, blockIdx.y * 32);
 }
 
 __global__ void tc_mean_kernel(const float* __restrict__ X, int n, int p, int ldx, float* mu) {
@@ -197,34 +179,59 @@ __global__ void tc_mean_kernel(const float* __restrict__ X, int n, int p, int ld
                         gridDim.x * blockDim.x);
 }
 
-// Tiles of 128 rows x BN columns holding an entry with column >= row:
-// row block tm keeps column blocks tn >= (128 tm) / BN.  Tiles are numbered
-// row block by row block.
-struct TileGrid {
-    int tm_count, tn_count, bn;
-    __host__ __device__ int first_tn(int tm) const { return (TC_BM * tm) / bn; }
-    __host__ __device__ int count() const {
-        int c = 0;
-        for (int tm = 0; tm < tm_count; ++tm) c += tn_count - first_tn(tm);
-        return c;
-    }
-    __device__ void coords(int idx, int& tm, int& tn) const {
-        int r = 0;
-        for (; r < tm_count - 1; ++r) {
-            const int c = tn_count - first_tn(r);
-            if (idx < c) break;
-            idx -= c;
-        }
-        tm = r;
-        tn = first_tn(r) + idx;
-    }
+// Where one tile's operands and output are.
+struct TcJob {
+    const CUtensorMap* mh;
+    const CUtensorMap* ml;
+    float* S;
+    int lds, p, m0, n0, KT;
+    float inv_n;
 };
 
-template <int BN, int KB, int STAGES>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    gram_tc_kernel(const __grid_constant__ CUtensorMap map_h,
-                   const __grid_constant__ CUtensorMap map_l, int p, int n_pad, float inv_n,
-                   float* __restrict__ S, int lds, TileGrid grid_tiles, int n_tiles) {
+template <int KB>
+__device__ __forceinline__ void make_job(const TcFit& f, int local, TcJob& j) {
+    int tm, tn;
+    f.g.coords(local, tm, tn);
+    j.mh = &f.mh;
+    j.ml = &f.ml;
+    j.S = f.S;
+    j.lds = f.lds;
+    j.p = f.p;
+    j.m0 = tm * TC_BM;
+    j.n0 = tn * f.g.bn;
+    j.KT = f.n_pad / KB;
+    j.inv_n = f.inv_n;
+}
+
+// Tile source of one fit: the fit (and its tensor maps) in the kernel's
+// parameter space.
+struct TcOne {
+    TcFit f;
+    int n_tiles;
+    static constexpr bool kTableMaps = false;
+    __device__ int tiles() const { return n_tiles; }
+    __device__ int fit_index(int) const { return 0; }
+    __device__ const TcFit& fit_at(int) const { return f; }
+};
+
+// Tile source of a batch: a table of fits and the fit of every tile, in
+// global memory.
+struct TcMany {
+    const TcFit* fits;
+    const int* tile_fit;
+    int n_tiles;
+    static constexpr bool kTableMaps = true;
+    __device__ int tiles() const { return n_tiles; }
+    __device__ int fit_index(int tile) const { return __ldg(tile_fit + tile); }
+    __device__ const TcFit& fit_at(int fi) const { return fits[fi]; }
+};
+
+// Slots of the per-tile K-block counts the producer hands to the MMA issuer
+// (the producer runs at most STAGES K blocks, so at most STAGES tiles, ahead).
+constexpr int TC_RING = 8;
+
+template <int BN, int KB, int STAGES, class Src>
+__global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const __grid_constant__ Src src) {
     using C = TcCfg<BN, KB, STAGES>;
     extern __shared__ unsigned char smem_dyn[];
     // 1024-byte alignment for the swizzled operand tiles
@@ -242,9 +249,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     volatile int* fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* issued_slot = fail + 1;       // K blocks whose loads were issued
     volatile int* consumed_slot = fail + 2;     // K blocks whose loads the MMA issuer saw land
+    volatile int* kt_ring = fail + 4;           // K blocks of the CTA's i-th tile at [i % TC_RING]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int KT = n_pad / KB;
+    const int n_tiles = src.tiles();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -260,8 +268,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         *issued_slot = 0;
         *consumed_slot = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_h)));
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_l)));
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -278,11 +284,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             // producer
             int kb = 0;      // K blocks issued by this CTA over all its tiles
-            for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x) {
-                int tm, tn;
-                grid_tiles.coords(tile, tm, tn);
-                const int m0 = tm * TC_BM, n0 = tn * BN;
-                for (int kt = 0; kt < KT; ++kt, ++kb) {
+            const TcFit* last = nullptr;
+            int fi_next = blockIdx.x < n_tiles ? src.fit_index(blockIdx.x) : 0;
+            int li = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x, ++li) {
+                const int fi = fi_next;
+                // the next tile's fit is read while this tile's copies run
+                if (tile + (int)gridDim.x < n_tiles) fi_next = src.fit_index(tile + gridDim.x);
+                const TcFit& f = src.fit_at(fi);
+                TcJob jb;
+                make_job<KB>(f, tile - f.tile_start, jb);
+                kt_ring[li % TC_RING] = jb.KT;      // published by the first expect_tx below
+                if (Src::kTableMaps && &f != last) {
+                    // maps written to global memory before the launch: order
+                    // those writes before the copies that read the maps
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                     reinterpret_cast<unsigned long long>(jb.mh))
+                                 : "memory");
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                     reinterpret_cast<unsigned long long>(jb.ml))
+                                 : "memory");
+                    last = &f;
+                }
+                const int m0 = jb.m0, n0 = jb.n0;
+                for (int kt = 0; kt < jb.KT; ++kt, ++kb) {
                     const int s = kb % STAGES;
                     if (kb >= STAGES &&
                         !mbar_wait(smem_u32(&empty[s]), ((kb / STAGES) - 1) & 1, fail)) {
@@ -293,14 +318,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     unsigned char* st = stages + (size_t)s * C::STAGE_BYTES;
                     mbar_expect_tx(fb, C::STAGE_BYTES);
                     const int x = kt * KB;
-                    tma_load_2d(smem_u32(st), &map_h, x, m0, fb);
-                    tma_load_2d(smem_u32(st + C::A_BYTES), &map_l, x, m0, fb);
+                    tma_load_2d(smem_u32(st), jb.mh, x, m0, fb);
+                    tma_load_2d(smem_u32(st + C::A_BYTES), jb.ml, x, m0, fb);
                     unsigned char* bh = st + 2 * C::A_BYTES;
                     unsigned char* bl = bh + C::B_BYTES;
 #pragma unroll
                     for (int h = 0; h < BN / TC_BM; ++h) {
-                        tma_load_2d(smem_u32(bh + h * C::A_BYTES), &map_h, x, n0 + h * TC_BM, fb);
-                        tma_load_2d(smem_u32(bl + h * C::A_BYTES), &map_l, x, n0 + h * TC_BM, fb);
+                        tma_load_2d(smem_u32(bh + h * C::A_BYTES), jb.mh, x, n0 + h * TC_BM, fb);
+                        tma_load_2d(smem_u32(bl + h * C::A_BYTES), jb.ml, x, n0 + h * TC_BM, fb);
                     }
                     *issued_slot = kb + 1;
                 }
@@ -319,12 +344,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const unsigned d = tmem + (unsigned)(b * BN);
+                int KT = 1;                  // read once the tile's first K block has landed
                 for (int kt = 0; kt < KT; ++kt, ++kb) {
                     const int s = kb % STAGES;
                     if (!mbar_wait(smem_u32(&full[s]), (kb / STAGES) & 1, fail)) {
                         ok = false;
                         break;
                     }
+                    if (kt == 0) KT = kt_ring[local % TC_RING];
                     *consumed_slot = kb + 1;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const unsigned base = smem_u32(stages + (size_t)s * C::STAGE_BYTES);
@@ -357,13 +384,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int q = warp & 3, half = ew >> 2;
         // 32 x 32 floats, row j at 32 j, its 16-byte groups XOR-swizzled by j
         float4* buf = reinterpret_cast<float4*>(epi + ew * C::EPI_FLOATS);
-        const bool vec = (lds & 3) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
         bool ok = true;
         int local = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++local) {
-            int tm, tn;
-            grid_tiles.coords(tile, tm, tn);
-            const int m0 = tm * TC_BM + 32 * q, n0 = tn * BN;
+            TcJob jb;
+            {
+                const TcFit& f = src.fit_at(src.fit_index(tile));
+                make_job<KB>(f, tile - f.tile_start, jb);
+            }
+            const int m0 = jb.m0 + 32 * q, n0 = jb.n0, p = jb.p, lds = jb.lds;
+            float* __restrict__ S = jb.S;
+            const float inv_n = jb.inv_n;
+            const bool vec = (lds & 3) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
             const int b = local & 1, u = local >> 1;
             if (ok) {
                 int got = 0;
@@ -463,60 +495,71 @@ EncodeTiled encoder() {
     return fn;
 }
 
-constexpr int TC_NPAD = 64;
-int pad_n(int n) { return (n + TC_NPAD - 1) / TC_NPAD * TC_NPAD; }
-
 // Operand maps over XhT / XlT ([p][n_pad] bf16): boxes of KB x 128 rows.
 template <int KB>
-bool encode_maps(EncodeTiled enc, CUtensorMap& mh, CUtensorMap& ml, void* XhT, void* XlT, int p,
-                 int n_pad) {
+bool encode_maps(EncodeTiled enc, CUtensorMap& mh, CUtensorMap& ml, const void* XhT,
+                 const void* XlT, int p, int n_pad) {
     const cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)p};
     const cuuint64_t strides[1] = {(cuuint64_t)n_pad * 2};
     const cuuint32_t box[2] = {(cuuint32_t)KB, (cuuint32_t)TC_BM};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapSwizzle swz = KB == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-    return enc(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XhT, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    return enc(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(XhT), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
-           enc(&ml, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XlT, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           enc(&ml, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(XlT), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int KB, int STAGES>
-cudaError_t launch_tiles(EncodeTiled enc, void* XhT, void* XlT, int n, int p, int n_pad, float* S,
-                         int lds, cudaStream_t st) {
-    using C = TcCfg<BN, KB, STAGES>;
-    CUtensorMap mh, ml;
-    if (!encode_maps<KB>(enc, mh, ml, XhT, XlT, p, n_pad)) return cudaErrorInvalidValue;
-    auto kern = gram_tc_kernel<BN, KB, STAGES>;
+constexpr int TC_KB = 64;             // K block of every launch (128-byte swizzle)
+
+bool fill_fit(EncodeTiled enc, TcFit& f, const void* XhT, const void* XlT, int n, int p, float* S,
+              int lds, int tile_start, int bn) {
+    f = TcFit{};
+    f.n_pad = tc_pad_n(n);
+    if (!encode_maps<TC_KB>(enc, f.mh, f.ml, XhT, XlT, p, f.n_pad)) return false;
+    f.S = S;
+    f.p = p;
+    f.lds = lds;
+    f.tile_start = tile_start;
+    f.inv_n = (float)(1.0 / (double)n);
+    f.g = tc_tile_grid(p, bn);
+    return true;
+}
+
+int num_sms_now() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
+template <int BN, int STAGES, class Src>
+cudaError_t launch_src(const Src& src, int n_tiles, cudaStream_t st) {
+    using C = TcCfg<BN, TC_KB, STAGES>;
+    auto kern = gram_tc_kernel<BN, TC_KB, STAGES, Src>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-        return e;
-    TileGrid g{(p + TC_BM - 1) / TC_BM, (p + BN - 1) / BN, BN};
-    const int n_tiles = g.count();
+    const int sms = num_sms_now();
+    if (sms <= 0) return cudaErrorInvalidDevice;
+    if (n_tiles <= 0) return cudaSuccess;
     const int grid = n_tiles < sms ? n_tiles : sms;
-    kern<<<grid, TC_THREADS, C::SMEM, st>>>(mh, ml, p, n_pad, (float)(1.0 / (double)n), S, lds, g,
-                                            n_tiles);
+    kern<<<grid, TC_THREADS, C::SMEM, st>>>(src);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t gram_tc_ws_bytes(int n, int p) {
-    const size_t np = (size_t)pad_n(n);
-    return align_up((size_t)p * 4, 256) + 2 * align_up((size_t)p * np * 2, 256);
-}
+size_t gram_tc_ws_bytes(int n, int p) { return align_up((size_t)p * 4, 256) + tc_operand_bytes(n, p); }
 
 cudaError_t launch_gram_tc(const float* X, int n, int p, int ldx, int center, float* S, int lds,
                            void* ws, cudaStream_t st) {
     EncodeTiled enc = encoder();
     if (!enc) return cudaErrorNotSupported;
-    const int n_pad = pad_n(n);
+    const int n_pad = tc_pad_n(n);
     unsigned char* base = static_cast<unsigned char*>(ws);
     float* mu = reinterpret_cast<float*>(base);
     __nv_bfloat16* XhT = reinterpret_cast<__nv_bfloat16*>(base + align_up((size_t)p * 4, 256));
@@ -530,8 +573,25 @@ cudaError_t launch_gram_tc(const float* X, int n, int p, int ldx, int center, fl
     // bandwidth; two 96 KB stages of 128-byte-swizzled K blocks of 64 ran
     // faster than four 48 KB stages of 64-byte-swizzled blocks of 32.  Small
     // p keeps 128-column tiles for more tiles per SM.
-    if (p > 1024) return launch_tiles<256, 64, 2>(enc, XhT, XlT, n, p, n_pad, S, lds, st);
-    return launch_tiles<128, 64, 3>(enc, XhT, XlT, n, p, n_pad, S, lds, st);
+    const int bn = p > 1024 ? 256 : 128;
+    TcOne one;
+    if (!fill_fit(enc, one.f, XhT, XlT, n, p, S, lds, 0, bn)) return cudaErrorInvalidValue;
+    one.n_tiles = one.f.g.count();
+    if (bn == 256) return launch_src<256, 2>(one, one.n_tiles, st);
+    return launch_src<128, 3>(one, one.n_tiles, st);
+}
+
+bool tc_encode_fit(TcFit& f, const void* XhT, const void* XlT, int n, int p, float* S, int lds,
+                   int tile_start, int bn) {
+    EncodeTiled enc = encoder();
+    return enc && fill_fit(enc, f, XhT, XlT, n, p, S, lds, tile_start, bn);
+}
+
+cudaError_t launch_gram_tc_batch(const TcFit* fits, const int* tile_fit, int n_tiles,
+                                 cudaStream_t st) {
+    static_assert(TC_BATCH_BN == 128, "the batched launch is instantiated for 128-column tiles");
+    TcMany many{fits, tile_fit, n_tiles};
+    return launch_src<128, 3>(many, n_tiles, st);
 }
 
 }  // namespace spmesl

@@ -121,3 +121,77 @@ def test_mixed_batch_256_fits():
             res = compare_theta(T1, ref["Theta"], ref["B"], ref["sigma"])
             assert res["ok"], (i, res)
     bt.close()
+
+
+# Split-BF16 tensor-core Gram inside the batch (SPMESL_MIXED): one batched
+# split/transpose launch and one persistent tcgen05 launch over the tiles of
+# all fits.  Each fit must equal the single-fit mixed path (spmesl_gram +
+# spmesl_fit with SPMESL_MIXED) bit for bit and match the FP64 oracle.
+MIXED = SMALL + [dict(kind="hub_scaled", p=300, n=129, seed=7), dict(kind="er", p=1025, n=65, seed=8),
+                 dict(kind="ar1", p=1300, n=200, seed=9)]
+
+
+@pytest.mark.parametrize("center", [False, True])
+def test_mixed_batch_equals_single_mixed_fits_and_oracle(center):
+    probs, inputs = _problems(MIXED, np.float32)
+    if center:
+        inputs = [(X + 0.25, lam) for X, lam in inputs]
+    bt = sp.Batch(inputs, kind="X", precision="mixed", tol=1e-6, center=center)
+    bt.run()
+    statuses, st = bt.result()
+    assert all(s == sp.SPMESL_OK for s in statuses), statuses
+    for i, (pr, (X, lam)) in enumerate(zip(probs, inputs)):
+        S = sp.gram(X, precision="mixed", center=center)
+        T1, s1, _ = sp.fit(S, lam, tol=1e-6, precision="mixed")
+        assert torch.equal(bt.Theta[i], T1) and torch.equal(bt.sigma[i], s1), i
+        Xn = (pr.X + np.float32(0.25)) if center else pr.X
+        ref = oracle.spmesl(oracle.gram(Xn.astype(np.float64), center=center), lam, tol=1e-6,
+                            maxit=1000)
+        res = compare_theta(bt.Theta[i].cpu().numpy(), ref["Theta"], ref["B"], ref["sigma"])
+        assert res["ok"], (i, res)
+    bt.close()
+
+
+def test_mixed_batch_graph_replay_and_bad_fit():
+    probs, inputs = _problems(MIXED[:4], np.float32)
+    bad = inputs[2][0].clone()
+    bad[1, 2] = float("nan")
+    inputs[2] = (bad, inputs[2][1])
+    plain = sp.Batch(inputs, kind="X", precision="mixed")
+    plain.run()
+    st_plain, _ = plain.result()
+    assert st_plain[2] == sp.SPMESL_ENONFINITE
+    assert all(s == sp.SPMESL_OK for k, s in enumerate(st_plain) if k != 2)
+    graphed = sp.Batch(inputs, kind="X", precision="mixed", use_graph=True)
+    for _ in range(3):                  # capture, then replays
+        graphed.run()
+        statuses, _ = graphed.result()
+        assert statuses == st_plain
+        for k, (a, b) in enumerate(zip(plain.Theta, graphed.Theta)):
+            if k != 2:
+                assert torch.equal(a, b)
+    plain.close()
+    graphed.close()
+
+
+def test_mixed_precision_batch_256_fits():
+    """The 256-fit batch with the tensor-core Gram: every fit equals its
+    single-fit mixed run and a sample matches the oracle."""
+    specs = synth.batch_specs(256)
+    probs, inputs = _problems(specs, np.float32)
+    bt = sp.Batch(inputs, kind="X", precision="mixed", use_graph=True)
+    bt.run()
+    statuses, st = bt.result()
+    assert all(s in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED) for s in statuses)
+    rng = np.random.default_rng(1)
+    sample = set(rng.choice(256, 8, replace=False).tolist())
+    for i, (pr, (X, lam)) in enumerate(zip(probs, inputs)):
+        S = sp.gram(X, precision="mixed")
+        T1, s1, _ = sp.fit(S, lam, tol=1e-6, precision="mixed")
+        assert torch.equal(bt.Theta[i], T1), i
+        if i in sample:
+            ref = oracle.spmesl(oracle.gram(pr.X.astype(np.float64)), lam, tol=1e-6, maxit=1000,
+                                nthreads=0)
+            res = compare_theta(T1.cpu().numpy(), ref["Theta"], ref["B"], ref["sigma"])
+            assert res["ok"], (i, res)
+    bt.close()
