@@ -535,7 +535,7 @@ def run_serve(args):
     tol, maxit = 1e-6, 1000
 
     def serve_run(rate):
-        srv = sp.Server(120 << 30, max_slots=256, precision="fp32", tol=tol, maxit=maxit)
+        srv = sp.Server(120 << 30, max_slots=256, precision=BATCH_PREC, tol=tol, maxit=maxit)
         gaps = rng.exponential(1.0 / rate, R) if rate else np.zeros(R)
         arrivals = np.cumsum(gaps)
         t0 = time.perf_counter()
@@ -616,7 +616,8 @@ def run_serve(args):
     line = {"metric": METRIC, "workload": "serve",
             "config": {"requests": R, "datasets": len(pool), "p": "log-uniform [100, 5000]",
                        "n": "max(p/4, 50)", "networks": "ar1 / er / hub_scaled",
-                       "budget_gb": 120, "max_slots": 256, "precision": "fp32", "tol": tol,
+                       "budget_gb": 120, "max_slots": 256, "precision": BATCH_PREC,
+                       "plain_precision": "fp32", "tol": tol,
                        "arrivals": "Poisson, seed 7"},
             "saturation": {"served_solves_per_s": sat_serve, "plain_solves_per_s": sat_plain},
             "rates": rows, "unit": "solves/s; latency ms from arrival to completion"}

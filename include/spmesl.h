@@ -277,8 +277,12 @@ typedef struct {
 typedef struct spmesl_batch spmesl_batch;
 
 /* Plan a batch (host only: sizes, ordering, workspace layout).  The problems
- * are copied; tol and maxit apply to every fit.  opts: precision FP64 or FP32,
- * inner_rule must be SPMESL_INNER_COLUMN, standardize / center / lambda_rule /
+ * are copied; tol and maxit apply to every fit.  opts: precision FP64, FP32 or
+ * MIXED (FP32 data; the Gram of every fit given as X runs as split-BF16
+ * products on the tensor cores in one launch for the whole batch, the rest as
+ * in the single-fit mixed path, so each fit equals spmesl_gram + spmesl_fit
+ * with SPMESL_MIXED), inner_rule must be SPMESL_INNER_COLUMN,
+ * standardize / center / lambda_rule /
  * warps_per_block / use_graph as documented in spmesl_opts.
  * Errors: EINVAL (no problems, p < 2 or above spmesl_max_p, missing
  * pointers, no usable lambda0), ENOMEM (host allocation). */
@@ -322,8 +326,8 @@ void spmesl_batch_destroy(spmesl_batch* batch);
  * does not depend on what it was batched with.  The paper has no serving
  * system; each request is the fit of Algorithm 2.
  *
- * spmesl_ctx_create: tol / maxit apply to every request; opts: precision FP64
- *   or FP32 (inner_rule COLUMN), other fields as for spmesl_batch_create.
+ * spmesl_ctx_create: tol / maxit apply to every request; opts: precision FP64,
+ *   FP32 or MIXED (inner_rule COLUMN), other fields as for spmesl_batch_create.
  *   Uses the current device.  Errors: EINVAL, ENOMEM, ECUDA.
  * spmesl_submit: `request` (an spmesl_problem: device pointers that must stay
  *   valid until the request completes; lambda0 <= 0 applies opts->lambda_rule)

@@ -231,10 +231,8 @@ __global__ void batch_theta_kernel(const BatchFit* __restrict__ fits,
     const int fi = find_fit(theta_prefix, count, blockIdx.x);
     const BatchFit& f = fits[fi];
     if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) return;
-    const int t = (f.p + 31) / 32;
-    const int idx = blockIdx.x - f.theta_start;
-    theta_tile<T>(static_cast<const T*>(f.BT), f.p, f.ldp, f.sigma, f.cs, f.Theta, f.sigma_out,
-                  f.ctrl, (idx / t) * 32, (idx % t) * 32);
+    theta_pair<T>(static_cast<const T*>(f.BT), f.p, f.ldp, f.sigma, f.cs, f.Theta, f.sigma_out,
+                  f.ctrl, blockIdx.x - f.theta_start);
 }
 
 // ---------------------------------------------------------------------------
@@ -588,8 +586,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
             gram += t * (t + 1) / 2;
         }
         f.theta_start = theta;
-        const int tt = (f.p + 31) / 32;
-        theta += tt * tt;
+        theta += o.precision == SPMESL_FP64 ? theta_pairs<double>(f.p) : theta_pairs<float>(f.p);
         b->max_ldp = std::max(b->max_ldp, f.ldp);
         b->max_p = std::max(b->max_p, f.p);
         b->max_n = std::max(b->max_n, f.n);

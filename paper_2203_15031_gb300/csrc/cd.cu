@@ -301,18 +301,18 @@ __global__ void prep_matrix_kernel(const T* __restrict__ S, int p, int ldp, cons
 // ---------------------------------------------------------------------------
 // Theta: Omega_1 = -B D on the working scale (Eq. (4)), min-magnitude
 // symmetrisation (Eq. (9); for j < k the tie keeps omega_jk) and
-// Omega^o = C Omega C (Proposition 1).  32x32 output tiles; the transposed
-// coefficient tile goes through shared memory so both reads are coalesced.
-// Also writes sigma in the original scale and counts nonzero b.
+// Omega^o = C Omega C (Proposition 1), over pairs of mirrored output tiles
+// whose coefficient tiles are read once into shared memory.  Also writes
+// sigma in the original scale and counts nonzero b.
 // ---------------------------------------------------------------------------
-// Theta for one fit: one block per 32 x 32 tile (see theta_tile).
+// Theta for one fit: one block per tile pair (see theta_pair).
 template <typename T>
 __global__ void theta_kernel(const T* __restrict__ BT, int p, int ldp,
                              const double* __restrict__ sigma, const double* __restrict__ cs,
                              double* __restrict__ Theta, double* __restrict__ sigma_out,
                              FitCtrl* ctrl) {
     if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
-    theta_tile<T>(BT, p, ldp, sigma, cs, Theta, sigma_out, ctrl, blockIdx.y * 32, blockIdx.x * 32);
+    theta_pair<T>(BT, p, ldp, sigma, cs, Theta, sigma_out, ctrl, blockIdx.x);
 }
 
 // B[j][k] = b_jk in the original scale: b^o_jk = b^C_jk c_j / c_k.
@@ -477,8 +477,7 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (f.phase_events) cudaEventRecord(f.phase_events[1], st);
 
-    dim3 tb(32, 8), tg((f.p + 31) / 32, (f.p + 31) / 32);
-    theta_kernel<T><<<tg, tb, 0, st>>>(a.BT, f.p, L.ldp, a.sigma,
+    theta_kernel<T><<<theta_pairs<T>(f.p), dim3(32, 8), 0, st>>>(a.BT, f.p, L.ldp, a.sigma,
                                        reinterpret_cast<const double*>(ws + L.cs), f.Theta,
                                        f.sigma_out, ctrl);
     if (f.phase_events) cudaEventRecord(f.phase_events[2], st);

@@ -340,6 +340,33 @@ __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, 
     const T cr = sizeof(T) == 4 ? (T)csf[r] : (T)cs[r];
     const T* __restrict__ srow = S + (size_t)r * p;
     T* __restrict__ out = SC + (size_t)r * ldp;
+    if constexpr (sizeof(T) == 4) {
+        // 16-byte accesses when the rows of S are 16-byte aligned (same arithmetic)
+        if ((p & 3) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
+            const float4* __restrict__ s4 = reinterpret_cast<const float4*>(srow);
+            const float4* __restrict__ c4 = reinterpret_cast<const float4*>(csf);
+            float4* __restrict__ o4 = reinterpret_cast<float4*>(out);
+            float4* __restrict__ g4 = GT ? reinterpret_cast<float4*>(GT + (size_t)r * ldp) : nullptr;
+            float4* __restrict__ b4 = BT ? reinterpret_cast<float4*>(BT + (size_t)r * ldp) : nullptr;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = tid; q < ldp / 4; q += nthr) {
+                float4 v = z;
+                if (4 * q < p) {                      // p % 4 == 0: the whole quad is inside
+                    const float4 s = s4[q], cc = c4[q];
+                    bad |= !isfinite(s.x) || !isfinite(s.y) || !isfinite(s.z) || !isfinite(s.w);
+                    v = make_float4(s.x * cr * cc.x, s.y * cr * cc.y, s.z * cr * cc.z,
+                                    s.w * cr * cc.w);
+                    const int d = r - 4 * q;
+                    if (d >= 0 && d < 4)
+                        diag[r] = d == 0 ? v.x : d == 1 ? v.y : d == 2 ? v.z : v.w;
+                }
+                o4[q] = v;
+                if (g4) g4[q] = v;
+                if (b4) b4[q] = z;
+            }
+            return bad;
+        }
+    }
     for (int c = tid; c < ldp; c += nthr) {
         T v = T(0);
         if (c < p) {
@@ -750,67 +777,136 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
     return true;
 }
 
-// One 32 x 32 tile (rows j0.., columns k0..) of Theta: Omega_1 = -B D on the
-// working scale (Eq. (4)), min-magnitude symmetrisation (Eq. (9); for j < k a
-// tie keeps omega_jk) and Omega^o = C Omega C (Proposition 1).  The
-// transposed coefficient tile goes through shared memory so both reads are
-// coalesced.  Blocks of the tile row j0 = 0 also write sigma in the original
-// scale; nonzero coefficients are counted into ctrl->nnz.  Block shape 32 x 8.
+// Theta (Eq. (4), Eq. (9), Proposition 1) over pairs of TS x TS tiles: the
+// tile of rows j0.., columns k0.. (j0 <= k0) and its mirror.  Omega_1 = -B D
+// on the working scale, min-magnitude symmetrisation (for j < k a tie keeps
+// omega_jk) and Omega^o = C Omega C.  Both coefficient tiles are read once
+// into shared memory; one pass writes the tile and a second its mirror, each
+// with rows of TS consecutive doubles.  Every value is computed from the same
+// (j, k) in both passes, so Theta is exactly symmetric.  Blocks of the first
+// tile row also write sigma in the original scale; nonzero coefficients are
+// counted into ctrl->nnz.  Block shape 32 x 8.  TS = 64 for FP32
+// coefficients, 32 for FP64 (static shared memory).
 template <typename T>
-__device__ void theta_tile(const T* __restrict__ BT, int p, int ldp,
-                          const double* __restrict__ sigma, const double* __restrict__ cs,
-                          double* __restrict__ Theta, double* __restrict__ sigma_out,
-                          FitCtrl* ctrl, int j0, int k0) {
-    __shared__ T tileA[32][33];   // tileA[kk][jj] = BT[k0+kk][j0+jj] = b_{j,k}
-    // 1/sigma^2 and c for the tile's 32 columns k and 32 rows j: FP64
-    // divisions are expensive on this part, so each block does 64 of them
-    // instead of one per element
-    __shared__ double inv_k[32], inv_j[32], c_k[32], c_j[32];
+__host__ __device__ constexpr int theta_ts() { return sizeof(T) == 4 ? 64 : 32; }
+
+// Tile pairs of a p x p Theta.
+template <typename T>
+__host__ __device__ inline int theta_pairs(int p) {
+    const int t = (p + theta_ts<T>() - 1) / theta_ts<T>();
+    return t * (t + 1) / 2;
+}
+
+template <typename T>
+__device__ void theta_pair(const T* __restrict__ BT, int p, int ldp,
+                           const double* __restrict__ sigma, const double* __restrict__ cs,
+                           double* __restrict__ Theta, double* __restrict__ sigma_out,
+                           FitCtrl* ctrl, int pair) {
+    constexpr int TS = theta_ts<T>();
+    __shared__ T tA[TS][TS + 1];    // tA[kk][jj] = BT[k0+kk][j0+jj] = b_jk
+    __shared__ T tB[TS][TS + 1];    // tB[jj][kk] = BT[j0+jj][k0+kk] = b_kj
+    // 1/sigma^2 and c for the pair's rows and columns: FP64 divisions are
+    // expensive on this part, so each block does 2 TS of them
+    __shared__ double inv_j[TS], inv_k[TS], c_j[TS], c_k[TS];
+    const int t = (p + TS - 1) / TS;
+    int a = 0, rem = pair;
+    while (rem >= t - a) {
+        rem -= t - a;
+        ++a;
+    }
+    const int j0 = a * TS, k0 = (a + rem) * TS;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    if (ty < 2) {
-        const int i = (ty == 0 ? k0 : j0) + tx;
+    const int lin = ty * 32 + tx;
+    if (lin < 2 * TS) {
+        const bool col = lin < TS;
+        const int i = col ? k0 + lin : j0 + lin - TS;
         double inv = 0.0, c = 0.0;
         if (i < p) {
             const double s = sigma[i];
             inv = 1.0 / (s * s);
             c = cs[i];
         }
-        if (ty == 0) { inv_k[tx] = inv; c_k[tx] = c; }
-        else { inv_j[tx] = inv; c_j[tx] = c; }
+        if (col) { inv_k[lin] = inv; c_k[lin] = c; }
+        else { inv_j[lin - TS] = inv; c_j[lin - TS] = c; }
     }
-    for (int rr = ty; rr < 32; rr += 8) {
-        const int k = k0 + rr, j = j0 + tx;
-        tileA[rr][tx] = (k < p && j < p) ? BT[(size_t)k * ldp + j] : T(0);
+    if constexpr (sizeof(T) == 4) {
+        // 16-byte reads: 16 lanes per 64-float row; columns p..ldp-1 of B are
+        // zero, quads past the padded row are not read
+        const int q = 4 * (tx & 15);
+        for (int r = 2 * ty + (tx >> 4); r < TS; r += 16) {
+            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+            if (k0 + r < p && j0 + q < ldp) va = *reinterpret_cast<const float4*>(BT + (size_t)(k0 + r) * ldp + j0 + q);
+            if (j0 + r < p && k0 + q < ldp) vb = *reinterpret_cast<const float4*>(BT + (size_t)(j0 + r) * ldp + k0 + q);
+            tA[r][q] = va.x; tA[r][q + 1] = va.y; tA[r][q + 2] = va.z; tA[r][q + 3] = va.w;
+            tB[r][q] = vb.x; tB[r][q + 1] = vb.y; tB[r][q + 2] = vb.z; tB[r][q + 3] = vb.w;
+        }
+    } else {
+        for (int r = ty; r < TS; r += 8)
+            for (int q = tx; q < TS; q += 32) {
+                tA[r][q] = (k0 + r < p && j0 + q < p) ? BT[(size_t)(k0 + r) * ldp + j0 + q] : T(0);
+                tB[r][q] = (j0 + r < p && k0 + q < p) ? BT[(size_t)(j0 + r) * ldp + k0 + q] : T(0);
+            }
     }
     __syncthreads();
-    unsigned long long nnz = 0;
-    const int k = k0 + tx;
-    for (int rr = ty; rr < 32; rr += 8) {
-        const int j = j0 + rr;
-        if (j >= p || k >= p) continue;
+    // Theta_jk for j = j0 + jj, k = k0 + kk
+    auto value = [&](int jj, int kk) -> double {
+        const int j = j0 + jj, k = k0 + kk;
+        // the scale (c_j c_k) is formed before it multiplies, so the value
+        // does not depend on which of the pair computes it
+        if (j == k) return inv_k[kk] * (c_j[jj] * c_k[kk]);
+        const T bjk = tA[kk][jj];      // coefficient of x_j in regression k
+        const T bkj = tB[jj][kk];      // coefficient of x_k in regression j
+        if (bjk == T(0) && bkj == T(0)) return 0.0;   // both candidates are zero
+        const double ojk = -(double)bjk * inv_k[kk];  // Omega_1[j][k]
+        const double okj = -(double)bkj * inv_j[jj];  // Omega_1[k][j]
         double out;
-        if (j == k) {
-            out = inv_k[tx];
-        } else {
-            const T bjk = tileA[tx][rr];                       // coefficient of x_j in regression k
-            const T bkj = BT[(size_t)j * ldp + k];             // coefficient of x_k in regression j
-            nnz += (bkj != T(0));
-            if (bjk == T(0) && bkj == T(0)) {
-                out = 0.0;                                     // both candidates are zero
-            } else {
-                const double ojk = -(double)bjk * inv_k[tx];   // Omega_1[j][k]
-                const double okj = -(double)bkj * inv_j[rr];   // Omega_1[k][j]
-                if (j < k) out = fabs(ojk) > fabs(okj) ? okj : ojk;
-                else out = fabs(okj) > fabs(ojk) ? ojk : okj;  // pair (k, j) with k < j
-                out *= c_j[rr] * c_k[tx];
+        if (j < k) out = fabs(ojk) > fabs(okj) ? okj : ojk;
+        else out = fabs(okj) > fabs(ojk) ? ojk : okj;  // pair (k, j) with k < j
+        return out * (c_j[jj] * c_k[kk]);
+    };
+    unsigned long long nnz = 0;
+    if (TS == 64 && (p & 1) == 0 && (reinterpret_cast<uintptr_t>(Theta) & 15) == 0) {
+        // two consecutive entries per lane, 16-byte stores: a warp writes 64
+        // entries of a row (p even: p - 1 is odd, so an entry pair never
+        // straddles p)
+        const int e = 2 * tx;
+        for (int jj = ty; jj < TS; jj += 8) {              // the tile: rows j
+            const int j = j0 + jj, k = k0 + e;
+            if (j >= p || k >= p) continue;
+            nnz += (j != k && tB[jj][e] != T(0)) + (j != k + 1 && tB[jj][e + 1] != T(0));
+            *reinterpret_cast<double2*>(Theta + (size_t)j * p + k) =
+                make_double2(value(jj, e), value(jj, e + 1));
+        }
+        if (j0 != k0) {
+            for (int kk = ty; kk < TS; kk += 8) {          // the mirror: rows k
+                const int j = j0 + e, k = k0 + kk;
+                if (j >= p || k >= p) continue;
+                nnz += (tA[kk][e] != T(0)) + (tA[kk][e + 1] != T(0));
+                *reinterpret_cast<double2*>(Theta + (size_t)k * p + j) =
+                    make_double2(value(e, kk), value(e + 1, kk));
             }
         }
-        if (j == k) out *= c_j[rr] * c_k[tx];
-        // the scale (c_j c_k) is formed before it multiplies, so (j, k) and
-        // (k, j) get bit-identical values and the result is exactly symmetric
-        Theta[(size_t)j * p + k] = out;
+    } else {
+        // the tile: rows j, lanes along k
+        for (int jj = ty; jj < TS; jj += 8)
+            for (int kk = tx; kk < TS; kk += 32) {
+                const int j = j0 + jj, k = k0 + kk;
+                if (j >= p || k >= p) continue;
+                nnz += (j != k && tB[jj][kk] != T(0));
+                Theta[(size_t)j * p + k] = value(jj, kk);
+            }
+        // the mirror: rows k, lanes along j
+        if (j0 != k0) {
+            for (int kk = ty; kk < TS; kk += 8)
+                for (int jj = tx; jj < TS; jj += 32) {
+                    const int j = j0 + jj, k = k0 + kk;
+                    if (j >= p || k >= p) continue;
+                    nnz += (tA[kk][jj] != T(0));
+                    Theta[(size_t)k * p + j] = value(jj, kk);
+                }
+        }
     }
-    if (j0 == 0 && ty == 0 && k < p) sigma_out[k] = sigma[k] / cs[k];
+    if (j0 == 0 && lin < TS && k0 + lin < p) sigma_out[k0 + lin] = sigma[k0 + lin] / cs[k0 + lin];
     // one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(FULL_MASK, nnz, o);

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gram_tc.cuh"
 
 namespace {
 
@@ -76,6 +77,9 @@ size_t request_bytes(const spmesl_problem& q, int precision) {
     size_t b = 256 + 2 * spmesl::align_up((size_t)q.p * 8, 256) + spmesl::align_up((size_t)q.p * 4, 256) * 2 +
                2 * spmesl::align_up((size_t)q.p * s, 256);
     if (q.X) b += spmesl::align_up((size_t)q.p * q.p * s, 256) + spmesl::align_up((size_t)q.p * s, 256);
+    if (q.X && precision == SPMESL_MIXED)    // bf16 operands, tensor-map entry, tile-to-fit slots
+        b += spmesl::tc_operand_bytes(q.n, q.p) + sizeof(spmesl::TcFit) +
+             4 * (size_t)spmesl::tc_tile_grid(q.p, spmesl::TC_BATCH_BN).count() + 512;
     b += 2 * spmesl::align_up((size_t)q.p * ldp * s, 256);
     b += 4096;                            // share of descriptors and queues
     return b;
@@ -243,7 +247,8 @@ spmesl_status spmesl_ctx_create(spmesl_ctx** out, size_t mem_budget_bytes, int m
     if (!c) return SPMESL_ENOMEM;
     if (opts) c->opts = *opts;
     else spmesl_default_opts(&c->opts);
-    if (c->opts.precision != SPMESL_FP32 && c->opts.precision != SPMESL_FP64) {
+    if (c->opts.precision != SPMESL_FP32 && c->opts.precision != SPMESL_FP64 &&
+        c->opts.precision != SPMESL_MIXED) {
         delete c;
         return SPMESL_EINVAL;
     }

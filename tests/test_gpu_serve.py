@@ -45,9 +45,10 @@ SPECS = [dict(kind="er", p=120, n=60, seed=1), dict(kind="ar1", p=400, n=100, se
          dict(kind="hub_scaled", p=700, n=175, seed=7), dict(kind="ar1", p=50, n=30, seed=8)]
 
 
-def test_same_result_alone_and_in_the_mix():
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_same_result_alone_and_in_the_mix(prec):
     probs, Xs = _requests(SPECS)
-    srv = sp.Server(8 * GB, max_slots=64)
+    srv = sp.Server(8 * GB, max_slots=64, precision=prec)
     alone = []
     for pr, X in zip(probs, Xs):
         st, T, sg, info = _wait(srv, srv.submit(X, pr.lambda0))
@@ -59,8 +60,8 @@ def test_same_result_alone_and_in_the_mix():
         assert st == sp.SPMESL_OK
         assert torch.equal(T, alone[k][0]) and torch.equal(sg, alone[k][1]), k
         # and equal to the plain single-fit path
-        S = sp.gram(Xs[k], precision="fp32")
-        T1, s1, _ = sp.fit(S, probs[k].lambda0, tol=1e-6, precision="fp32")
+        S = sp.gram(Xs[k], precision=prec)
+        T1, s1, _ = sp.fit(S, probs[k].lambda0, tol=1e-6, precision=prec)
         assert torch.equal(T, T1) and torch.equal(sg, s1)
     srv.close()
 
