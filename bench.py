@@ -44,9 +44,10 @@ N_DATASETS = 10
 # the headline batched path: split-BF16 Gram on the tensor cores, CD in FP32,
 # sigma / convergence / Theta in FP64
 BATCH_PREC = "mixed"
-# per batched step: split/transpose, tcgen05 Gram, prep_diag, prep_matrix, lazy
-# cd, eager cd queue, theta (the FP32 path has one SIMT Gram launch instead of two)
-KERNELS_PER_SOLVE = {"mixed": 7, "fp32": 6}
+# per batched step: split/transpose, tcgen05 Gram, prep_diag, prep_matrix, column
+# order, lazy cd, eager cd queue, theta (the FP32 path has one SIMT Gram launch
+# instead of two)
+KERNELS_PER_SOLVE = {"mixed": 8, "fp32": 7}
 
 
 def _env_rank():

@@ -122,16 +122,48 @@ __global__ void batch_prep_diag_kernel(const BatchFit* __restrict__ fits, int st
 }
 
 // blockIdx.y = fit; blocks stride over the fit's rows (same arithmetic as
-// the single-fit prep_matrix_kernel), clearing BT on the way.
+// the single-fit prep_matrix_kernel), clearing BT on the way.  With heat,
+// also counts per column the off-diagonal entries of the standardised matrix
+// above lambda0: the coordinates that can move in the column's first sweep,
+// a predictor of how long the column takes.
 template <typename T>
-__global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits) {
+__global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits, int* __restrict__ heat) {
     const BatchFit& f = fits[blockIdx.y];
     bool bad = false;
-    for (int r = blockIdx.x; r < f.p; r += gridDim.x)
+    for (int r = blockIdx.x; r < f.p; r += gridDim.x) {
+        int cnt = 0;
         bad |= standardize_row<T>(static_cast<const T*>(f.S), f.p, f.ldp, r, f.cs, f.csf,
                                   static_cast<T*>(f.SC), nullptr, static_cast<T*>(f.BT),
-                                  static_cast<T*>(f.diag), threadIdx.x, blockDim.x);
+                                  static_cast<T*>(f.diag), threadIdx.x, blockDim.x,
+                                  (T)f.lambda0, heat ? &cnt : nullptr);
+        if (cnt) atomicAdd(&heat[f.col_start + r], cnt);
+    }
     if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
+}
+
+// Order of the coordinate-descent queue: all columns of the batch by
+// decreasing heat (counting sort, one block), so the longest column solves
+// start first instead of in the tail of the launch.  Ties in any order: a
+// column's result does not depend on when it runs.
+constexpr int HEAT_BINS = 64;
+__global__ void __launch_bounds__(1024) batch_order_kernel(const int* __restrict__ heat, int n,
+                                                          int* __restrict__ order) {
+    __shared__ int bin[HEAT_BINS];
+    const int t = threadIdx.x;
+    if (t < HEAT_BINS) bin[t] = 0;
+    __syncthreads();
+    for (int i = t; i < n; i += blockDim.x) atomicAdd(&bin[min(heat[i], HEAT_BINS - 1)], 1);
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int h = HEAT_BINS - 1; h >= 0; --h) {
+            const int c = bin[h];
+            bin[h] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < n; i += blockDim.x) order[atomicAdd(&bin[min(heat[i], HEAT_BINS - 1)], 1)] = i;
 }
 
 template <typename T>
@@ -203,14 +235,18 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
                                                             const int* __restrict__ col_prefix,
                                                             int count, int total_cols, int max_ldp,
                                                             double tol, int maxit,
-                                                            BatchHeader* hdr, int* ovf_list) {
+                                                            BatchHeader* hdr, int* ovf_list,
+                                                            const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)warp * lazy_warp_smem_bytes<T>(max_ldp);
     for (;;) {
         int gc = 0;
-        if (lane == 0) gc = atomicAdd(&hdr->next_col, 1);
+        if (lane == 0) {
+            gc = atomicAdd(&hdr->next_col, 1);
+            if (order && gc < total_cols) gc = order[gc];
+        }
         gc = __shfl_sync(FULL_MASK, gc, 0);
         if (gc >= total_cols) break;
         const int fi = find_fit(col_prefix, count, gc);
@@ -290,6 +326,7 @@ struct spmesl_batch {
     int warps_per_block = 0;       // 0 = automatic
     int gradient = SPMESL_GRADIENT_AUTO;
     size_t off_ovf = 0;            // queue of columns for the eager launch (total_cols ints)
+    size_t off_heat = 0, off_order = 0;   // per-column heat and the lazy queue's order
     std::vector<FitPlan> plan;     // ordered by decreasing p
     size_t off_hdr = 0, off_desc = 0, off_colp = 0, off_gramp = 0, off_thetap = 0, off_ctrls = 0;
     // SPMESL_MIXED: tensor-core Gram table, fit of every tile, split prefixes
@@ -349,7 +386,15 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
                                                                                    b->standardize);
     // rows per fit spread over blocks; enough blocks overall to fill the GPU
     const int mx = std::max(1, std::min(b->max_p, (num_sms() * 8 + count - 1) / count));
-    batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits);
+    // column order for the lazy launch (standardised working matrix only)
+    const bool lazy_order = b->gradient != SPMESL_GRADIENT_EAGER && b->standardize;
+    int* heat = reinterpret_cast<int*>(ws + b->off_heat);
+    int* order = reinterpret_cast<int*>(ws + b->off_order);
+    if (lazy_order &&
+        (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)b->total_cols, st)) != cudaSuccess)
+        return e;
+    batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits, lazy_order ? heat : nullptr);
+    if (lazy_order) batch_order_kernel<<<1, 1024, 0, st>>>(heat, b->total_cols, order);
 
     const size_t budget = (size_t)max_smem_block() - 1024;
     const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
@@ -372,7 +417,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
         lper_sm = std::max(lper_sm, 1);
         const int lgrid = std::min((b->total_cols + LW - 1) / LW, num_sms() * lper_sm);
         lk<<<lgrid, 32 * LW, lsm, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
-                                        b->maxit, hdr, ovf);
+                                        b->maxit, hdr, ovf, lazy_order ? order : nullptr);
     }
     // eager launch: every column, or only the queue the lazy launch left
     const size_t per_warp = warp_smem_bytes<T>(b->max_ldp);
@@ -597,6 +642,10 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->total_split = split;
     b->total_theta = theta;
     b->off_ovf = off;
+    off += align_up(sizeof(int) * (size_t)cols, 256);
+    b->off_heat = off;
+    off += align_up(sizeof(int) * (size_t)cols, 256);
+    b->off_order = off;
     off += align_up(sizeof(int) * (size_t)cols, 256);
     b->ws_bytes = off;
     if (spmesl::g_batch_pageable_staging) {

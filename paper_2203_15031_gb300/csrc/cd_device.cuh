@@ -335,7 +335,8 @@ __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, 
                                                 const float* __restrict__ csf,
                                                 T* __restrict__ SC, T* __restrict__ GT,
                                                 T* __restrict__ BT, T* __restrict__ diag, int tid,
-                                                int nthr) {
+                                                int nthr, T heat_lam = T(0), int* heat = nullptr) {
+    // heat (optional): this thread's count of off-diagonal |SC_rc| > heat_lam
     bool bad = false;
     const T cr = sizeof(T) == 4 ? (T)csf[r] : (T)cs[r];
     const T* __restrict__ srow = S + (size_t)r * p;
@@ -359,6 +360,9 @@ __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, 
                     const int d = r - 4 * q;
                     if (d >= 0 && d < 4)
                         diag[r] = d == 0 ? v.x : d == 1 ? v.y : d == 2 ? v.z : v.w;
+                    if (heat)
+                        *heat += (d != 0 && fabsf(v.x) > heat_lam) + (d != 1 && fabsf(v.y) > heat_lam) +
+                                 (d != 2 && fabsf(v.z) > heat_lam) + (d != 3 && fabsf(v.w) > heat_lam);
                 }
                 o4[q] = v;
                 if (g4) g4[q] = v;
@@ -375,6 +379,7 @@ __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, 
             const T cc = sizeof(T) == 4 ? (T)csf[c] : (T)cs[c];
             v = s * cr * cc;
             if (c == r) diag[r] = v;
+            else if (heat && fabs(v) > heat_lam) ++*heat;
         }
         out[c] = v;
         if (GT) GT[(size_t)r * ldp + c] = v;
