@@ -188,6 +188,20 @@ CD_SOURCES = ["paper_2203_15031_gb300/csrc/cd_device.cuh", "paper_2203_15031_gb3
 PROFILE = "profiles/batch_cd_lazy_kernel_er_p2000_n200_x10.md"
 
 
+def sweep_model(s, p, sweeps, moves, nnz_b, ms, hbm):
+    """Bytes of the row-synchronous schedule with G in memory, per launch:
+    every column sweep reads its p entries of G, every coordinate change
+    reads and writes a column of G and reads a row of S, and B is written.
+    The lazy kernel keeps no G and moves far fewer bytes, so at the bench
+    sizes (S in L2) this fraction compares the work done with what a
+    bandwidth-bound G schedule would need; it is not a traffic figure."""
+    b = float(s) * p * (sweeps + 3.0 * moves) + 2.0 * s * nnz_b
+    a = b / (ms / 1e3) / 1e9
+    return {"bytes_per_launch": b, "achieved": a, "frac": a / hbm,
+            "terms": "s*p*(column sweeps) + 2*s*p*moves + s*p*moves + 2*s*nnz(B)",
+            "column_sweeps": sweeps}
+
+
 def measured_traffic():
     """DRAM bytes per launch of the batched CD kernel from the committed ncu
     summary, or None when the kernel source changed since that capture."""
@@ -238,7 +252,7 @@ def run_ours(args):
             raise RuntimeError(f"warm-up fits did not converge: {statuses}")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        cd_ms, moves = [], []
+        cd_ms, moves, sweeps, nnzb = [], [], [], []
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -252,6 +266,8 @@ def run_ours(args):
             statuses, st = bt.result(stream)
             cd_ms.append(st["ms_cd"])
             moves.append(st["moves"])
+            sweeps.append(st["inner_sweeps"])
+            nnzb.append(st["nnz_B"])
         torch.cuda.synchronize()
         if sampler:
             sampler.__exit__(None, None, None)
@@ -263,12 +279,12 @@ def run_ours(args):
             t = torch.tensor([total_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
-        return bt, best_w, per, total_ms, cd_ms, moves
+        return bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb
 
     clk = ClockSampler(local_rank)
-    bt, best_w, per, total_ms, cd_ms, moves = batched(BATCH_PREC, clk)       # headline
+    bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb = batched(BATCH_PREC, clk)   # headline
     value = world * N_DATASETS * args.steps / (total_ms / 1e3)
-    bt32, _, per32, total32, _, _ = batched("fp32")
+    bt32, _, per32, total32, _, _, _, _ = batched("fp32")
     value32 = world * N_DATASETS * args.steps / (total32 / 1e3)
     bt32.close()
 
@@ -356,7 +372,9 @@ def run_ours(args):
                 "frac": achieved / hbm, "traffic": traffic,
                 "kernel": "batch_cd_lazy_kernel<float,1>", "peak_kind": which,
                 "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cd_mean_ms,
-                "moves_per_launch": mv, "warps_per_block": best_w}
+                "moves_per_launch": mv, "warps_per_block": best_w,
+                "sweep_model": sweep_model(4, p, statistics.mean(sweeps), mv,
+                                           statistics.mean(nnzb), cd_mean_ms, hbm)}
         srt = sorted(per)
         psrt = sorted(plain_per)
         q99 = lambda v: v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)]
@@ -448,7 +466,7 @@ def run_single(args):
     st = sp.Stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    gram_ms, cd_ms, moves = [], [], []
+    gram_ms, cd_ms, moves, sweeps, nnzb = [], [], [], [], []
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         for i in range(args.steps):
@@ -460,6 +478,8 @@ def run_single(args):
             gram_ms.append(g0.elapsed_time(g1))
             cd_ms.append(st.ms_cd)
             moves.append(st.moves)
+            sweeps.append(st.inner_sweeps)
+            nnzb.append(st.nnz_B)
         torch.cuda.synchronize()
     per = [a.elapsed_time(b) for a, b in ev]
     value = args.steps / (sum(per) / 1e3)
@@ -472,7 +492,9 @@ def run_single(args):
     roof = {"bound": "hbm", "achieved": bytes_cd / (cdm / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": bytes_cd / (cdm / 1e3) / 1e9 / hbm, "traffic": None,
             "kernel": "cd_column_lazy_kernel", "peak_kind": which,
-            "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cdm, "moves_per_launch": mv}
+            "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cdm, "moves_per_launch": mv,
+            "sweep_model": sweep_model(s, p, statistics.mean(sweeps), mv, statistics.mean(nnzb),
+                                       cdm, hbm)}
     gm = statistics.mean(gram_ms)
     roof_gram = None
     if prec == sp.MIXED:
@@ -625,6 +647,101 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_regression(args):
+    """One scaled-lasso regression per step (spmesl_scaled_lasso): Erdos-Renyi
+    predictors p=2000, n=200, y = X beta + noise with 10 active coefficients;
+    the split-BF16 Gram of [X y], then the response column's coordinate
+    descent.  The oracle (FP64 Gram of [X y] + Algorithm 1 for that column,
+    one thread) is timed beside it."""
+    import numpy as np
+    import torch
+
+    import paper_2203_15031_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sp.lib()
+    w = synth.REGRESSION
+    r = synth.make_regression(w["kind"], w["p"], w["n"], 0, k=w["k"], noise=w["noise"],
+                              dtype=w["dtype"])
+    p, n, tol, maxit = r.p, r.n, w["tol"], w["maxit"]
+    prec = {"fp64": sp.FP64, "fp32": sp.FP32, "mixed": sp.MIXED}[w["prec"]]
+    X, y = torch.from_numpy(r.X).to(dev), torch.from_numpy(r.y).to(dev)
+    beta = torch.empty(p, dtype=torch.float64, device=dev)
+    sigma = torch.empty(1, dtype=torch.float64, device=dev)
+    nb = sp.spmesl_scaled_lasso_workspace_bytes(n, p, prec)
+    keep, ws = sp._workspace(nb, dev)
+    opts = sp.spmesl_default_opts()
+    opts.precision = prec
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        sp._check(sp.spmesl_scaled_lasso(X, y, n, p, r.lambda0, tol, maxit, opts, beta, sigma,
+                                         None, ws, nb, stream), "spmesl_scaled_lasso")
+
+    for _ in range(args.warmup):
+        step()
+    st = sp.Stats()
+    rc = sp.spmesl_scaled_lasso(X, y, n, p, r.lambda0, tol, maxit, opts, beta, sigma, st, ws, nb,
+                                stream)
+    if rc != sp.SPMESL_OK:
+        raise RuntimeError(f"warm-up regression status {rc}")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    value = args.steps / (sum(per) / 1e3)
+    srt = sorted(per)
+    cb = None
+    acc = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        Z = np.concatenate([r.X.astype(np.float64), r.y.astype(np.float64)[:, None]], axis=1)
+        times = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            ref = oracle.columns(oracle.gram(Z), [p], r.lambda0, tol=tol, maxit=maxit, nthreads=1)
+            times.append(time.perf_counter() - t0)
+        tm = statistics.median(times)
+        cb = {"value": 1.0 / tm, "unit": "solves/s", "cores": 1, "kind": "oracle",
+              "sample": f"3 whole regressions (FP64 Gram of [X y] + Algorithm 1 for the response "
+                        f"column, one thread), median {tm:.3f} s"}
+        b_ref = ref["b"][0, :p]
+        acc = {"max_rel_dbeta_vs_fp64_oracle":
+               float(np.max(np.abs(beta.cpu().numpy() - b_ref)) / np.max(np.abs(b_ref))),
+               "rel_dsigma": abs(float(sigma.item()) - float(ref["sigma"][0])) / float(ref["sigma"][0])}
+    hbm, which = _peaks()
+    line = {"metric": "scaled-lasso regressions/s (spmesl_scaled_lasso)", "value": value,
+            "unit": "regressions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sum(per) / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "regression_er_p2000_n200", "p": p, "n": n,
+                       "active_coefficients": w["k"], "noise": w["noise"],
+                       "lambda0": "sqrt(2 log p / n)", "tol": tol, "maxit": maxit,
+                       "precision": w["prec"], "l2": "flushed between steps (256 MB write)"},
+            "latency": {"p50_ms": statistics.median(per),
+                        "p99_ms": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]},
+            "solve": {"outer_iters": st.outer_iters, "sweeps": st.inner_sweeps, "moves": st.moves,
+                      "nnz_beta": st.nnz_B},
+            "roofline": {"bound": "latency",
+                         "note": "one column solve is a single warp's dependent chain; the "
+                                 "Gram of [X y] is reported by --workload hub_p10000_n500_mixed"},
+            "accuracy": acc, "cpu_baseline": cb,
+            "gpu_launches": 8 * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    del keep
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -645,6 +762,8 @@ def main():
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "regression":
+        run_regression(args)
     elif args.workload != WORKLOAD:
         run_single(args)
     else:

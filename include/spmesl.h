@@ -235,6 +235,40 @@ spmesl_status spmesl_fit_coefficients(const void* workspace, int p, int precisio
                                       void* stream);
 
 /*
+ * One scaled-lasso regression (Section 2.1, Eq. (2); Algorithm 1): the joint
+ * minimiser over (beta, sigma > 0) of
+ *     ||y - X beta||^2 / (2 n sigma) + sigma / 2 + lambda0 ||beta||_1,
+ * with the predictors standardised when opts->standardize (the weighted
+ * penalty lambda0 sqrt(s_kk) |beta_k| of Proposition 1; beta and sigma are
+ * returned in the original scale), by cyclic coordinate descent with the
+ * alternating sigma update of Eq. (14).  It is one column problem of SPMESL:
+ * the Gram of [X y] is built (spmesl_gram, so SPMESL_MIXED uses the
+ * tensor-core Gram) and column p is solved.
+ *   X        n x p predictors, row-major (ld p), device, element type per
+ *            opts->precision (double for SPMESL_FP64, float otherwise).
+ *   y        n responses, device, same type.
+ *   lambda0  penalty level; with opts->lambda_rule != GIVEN the rule is
+ *            applied with (n, p) and lambda0 is ignored.
+ *   beta     p doubles (device), written on SPMESL_OK / NOT_CONVERGED /
+ *            EDEGENERATE; sigma: one double (device).
+ *   stats    optional host pointer; non-NULL synchronises `stream` and
+ *            fills the counters of the one column solve (nnz_B = nonzero
+ *            beta, ms_total = whole call).
+ *   workspace  spmesl_scaled_lasso_workspace_bytes(n, p, precision) bytes,
+ *            256-byte aligned, owned by the caller.
+ * opts: precision, standardize, center and lambda_rule are used; the inner
+ * rule is the per-column one and the gradient the lazy one.
+ * Errors: EINVAL (NULL pointers, n < 1, p < 1, p + 1 above spmesl_max_p,
+ * tol <= 0, maxit < 1, short or misaligned workspace, no usable lambda0),
+ * ENONFINITE (non-finite data), ECUDA.
+ */
+size_t spmesl_scaled_lasso_workspace_bytes(int n, int p, int precision);
+spmesl_status spmesl_scaled_lasso(const void* X, const void* y, int n, int p, double lambda0,
+                                  double tol, int maxit, const spmesl_opts* opts, double* beta,
+                                  double* sigma, spmesl_stats* stats, void* workspace,
+                                  size_t ws_bytes, void* stream);
+
+/*
  * End-to-end solve from HOST data: copies X_host to the device, builds S
  * (spmesl_gram), fits (spmesl_fit), copies Theta and sigma back to the host
  * buffers and synchronises `stream`.

@@ -25,6 +25,7 @@ __all__ = [
     "spmesl_default_opts", "spmesl_status_string", "spmesl_version", "spmesl_lambda",
     "spmesl_max_p", "spmesl_gram_workspace_bytes", "spmesl_gram", "spmesl_fit_workspace_bytes",
     "spmesl_fit", "spmesl_fit_noalloc", "spmesl_fit_result", "spmesl_fit_coefficients",
+    "spmesl_scaled_lasso_workspace_bytes", "spmesl_scaled_lasso",
     "spmesl_solve_workspace_bytes",
     "spmesl_solve", "spmesl_batch_create", "spmesl_batch_workspace_bytes", "spmesl_batch_run",
     "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_destroy", "Problem", "Batch",
@@ -97,6 +98,9 @@ _SIGS = {
                                   _vp, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_result": (_i32, [_vp, _i32, _i32, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_coefficients": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "spmesl_scaled_lasso_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "spmesl_scaled_lasso": (_i32, [_vp, _vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts),
+                                   _vp, _vp, ctypes.POINTER(Stats), _vp, _sz, _vp]),
     "spmesl_batch_create": (_i32, [ctypes.POINTER(Problem), _i32, _dbl, _i32,
                                    ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]),
     "spmesl_batch_workspace_bytes": (_sz, [_vp]),
@@ -242,6 +246,18 @@ def spmesl_fit_coefficients(workspace, p, precision, B, stream=None) -> int:
     return lib().spmesl_fit_coefficients(_ptr(workspace), p, precision, _ptr(B), _stream(stream))
 
 
+def spmesl_scaled_lasso_workspace_bytes(n: int, p: int, precision: int) -> int:
+    return lib().spmesl_scaled_lasso_workspace_bytes(n, p, precision)
+
+
+def spmesl_scaled_lasso(X, y, n, p, lambda0, tol, maxit, opts, beta, sigma, stats, workspace,
+                        ws_bytes, stream=None) -> int:
+    return lib().spmesl_scaled_lasso(_ptr(X), _ptr(y), n, p, lambda0, tol, maxit,
+                                     ctypes.byref(opts) if opts is not None else None, _ptr(beta),
+                                     _ptr(sigma), ctypes.byref(stats) if stats is not None else None,
+                                     _ptr(workspace), ws_bytes, _stream(stream))
+
+
 def spmesl_solve_workspace_bytes(n: int, p: int, precision: int) -> int:
     return lib().spmesl_solve_workspace_bytes(n, p, precision)
 
@@ -272,6 +288,34 @@ def gram(X, precision="fp32", center=False, stream=None):
     _check(spmesl_gram(X, n, p, p, prec, center, S, p, ws, nb, stream), "spmesl_gram")
     del keep
     return S
+
+
+def scaled_lasso(X, y, lambda0, tol=1e-6, maxit=1000, precision="fp32", standardize=True,
+                 center=False, lambda_rule=LAMBDA_GIVEN, stream=None):
+    """One scaled-lasso regression of CUDA tensor y (n) on X (n x p).
+    Synchronises and returns (beta (p, FP64), sigma (float), stats_dict)."""
+    import torch
+    _require_cuda()
+    prec = _prec(precision)
+    n, p = X.shape
+    X, y = X.contiguous(), y.contiguous()
+    beta = torch.empty(p, dtype=torch.float64, device=X.device)
+    sigma = torch.empty(1, dtype=torch.float64, device=X.device)
+    opts = spmesl_default_opts()
+    opts.precision = prec
+    opts.standardize = int(bool(standardize))
+    opts.center = int(bool(center))
+    opts.lambda_rule = int(lambda_rule)
+    nb = spmesl_scaled_lasso_workspace_bytes(n, p, prec)
+    keep, ws = _workspace(nb, X.device)
+    st = Stats()
+    rc = spmesl_scaled_lasso(X, y, n, p, lambda0, tol, maxit, opts, beta, sigma, st, ws, nb, stream)
+    del keep
+    if rc < 0:
+        raise SpmeslError(rc, "spmesl_scaled_lasso")
+    d = st.as_dict()
+    d["status"] = rc
+    return beta, float(sigma.item()), d
 
 
 def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=True,

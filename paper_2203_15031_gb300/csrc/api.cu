@@ -1,6 +1,8 @@
 // C ABI of libspmesl (declared in include/spmesl.h): argument validation,
 // workspace layout, stream-ordered launches and status reporting.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -93,6 +95,38 @@ spmesl_opts resolve_opts(const spmesl_opts* o) {
     spmesl_opts d;
     spmesl_default_opts(&d);
     return o ? *o : d;
+}
+
+// Workspace of spmesl_scaled_lasso: Z = [X y] (n x (p+1)), its Gram, the
+// Gram's scratch and the fit workspace of the (p+1)-column problem.
+struct LassoLayout {
+    size_t Z, S, gram, fit, total;
+};
+
+LassoLayout lasso_layout(int n, int p, int precision) {
+    const size_t s = (size_t)elem_size(precision);
+    const int q = p + 1;
+    LassoLayout L{};
+    size_t off = 0;
+    L.Z = off;    off += align_up((size_t)n * q * s, 256);
+    L.S = off;    off += align_up((size_t)q * q * s, 256);
+    L.gram = off; off += align_up(gram_ws_bytes(n, q, precision), 256);
+    L.fit = off;  off += fit_layout(q, precision).total;
+    L.total = off;
+    return L;
+}
+
+template <typename T>
+__global__ void augment_kernel(const T* __restrict__ X, const T* __restrict__ y, int n, int p,
+                               T* __restrict__ Z) {
+    const int q = p + 1;
+    const size_t total = (size_t)n * q;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / q;
+        const int c = (int)(i - r * q);
+        Z[i] = c < p ? X[r * p + c] : y[r];
+    }
 }
 
 }  // namespace
@@ -218,6 +252,86 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     stats->ms_fit = ms;
+    stats->lambda0 = lam;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rs;
+}
+
+size_t spmesl_scaled_lasso_workspace_bytes(int n, int p, int precision) {
+    if (n < 1 || p < 1 || !valid_precision(precision)) return 0;
+    return lasso_layout(n, p, precision).total;
+}
+
+spmesl_status spmesl_scaled_lasso(const void* X, const void* y, int n, int p, double lambda0,
+                                  double tol, int maxit, const spmesl_opts* opts, double* beta,
+                                  double* sigma, spmesl_stats* stats, void* workspace,
+                                  size_t ws_bytes, void* stream) {
+    const spmesl_opts o = resolve_opts(opts);
+    if (!X || !y || !beta || !sigma || !workspace || n < 1 || p < 1 || maxit < 1 ||
+        !(tol > 0.0) || !valid_precision(o.precision))
+        return SPMESL_EINVAL;
+    if (p + 1 > max_p_for(o.precision)) return SPMESL_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return SPMESL_EINVAL;
+    const LassoLayout L = lasso_layout(n, p, o.precision);
+    if (ws_bytes < L.total) return SPMESL_EINVAL;
+    double lam = lambda0;
+    if (o.lambda_rule != SPMESL_LAMBDA_GIVEN) lam = spmesl_lambda(o.lambda_rule, n, p);
+    if (!(lam > 0.0) || !isfinite(lam)) return SPMESL_EINVAL;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    const int q = p + 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+    }
+    const size_t total = (size_t)n * q;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+    if (o.precision == SPMESL_FP64)
+        augment_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(X),
+                                                     static_cast<const double*>(y), n, p,
+                                                     reinterpret_cast<double*>(ws + L.Z));
+    else
+        augment_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(X),
+                                                    static_cast<const float*>(y), n, p,
+                                                    reinterpret_cast<float*>(ws + L.Z));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_gram(ws + L.Z, n, q, q, o.precision, o.center, ws + L.S, q, ws + L.gram, st);
+    if (e == cudaSuccess) {
+        FitLaunch f;
+        f.S = ws + L.S;
+        f.p = q;
+        f.lambda0 = lam;
+        f.tol = tol;
+        f.maxit = maxit;
+        f.precision = o.precision;
+        f.standardize = o.standardize ? 1 : 0;
+        f.inner_rule = SPMESL_INNER_COLUMN;
+        f.warps_per_block = 0;
+        f.gradient = SPMESL_GRADIENT_LAZY;
+        f.Theta = nullptr;
+        f.sigma_out = sigma;
+        f.ws = ws + L.fit;
+        f.phase_events = nullptr;
+        f.response_col = p;
+        f.beta_out = beta;
+        e = launch_fit(f, st);
+    }
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return from_cuda(e);
+    }
+    if (!stats) return SPMESL_OK;
+    cudaEventRecord(e1, st);
+    spmesl_status rs = spmesl_fit_result(ws + L.fit, q, o.precision, stats, stream);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    stats->ms_total = ms;
     stats->lambda0 = lam;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

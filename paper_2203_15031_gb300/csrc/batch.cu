@@ -141,30 +141,7 @@ __global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits, int*
     if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
 }
 
-// Order of the coordinate-descent queue: all columns of the batch by
-// decreasing heat (counting sort, one block), so the longest column solves
-// start first instead of in the tail of the launch.  Ties in any order: a
-// column's result does not depend on when it runs.
-constexpr int HEAT_BINS = 64;
-__global__ void __launch_bounds__(1024) batch_order_kernel(const int* __restrict__ heat, int n,
-                                                          int* __restrict__ order) {
-    __shared__ int bin[HEAT_BINS];
-    const int t = threadIdx.x;
-    if (t < HEAT_BINS) bin[t] = 0;
-    __syncthreads();
-    for (int i = t; i < n; i += blockDim.x) atomicAdd(&bin[min(heat[i], HEAT_BINS - 1)], 1);
-    __syncthreads();
-    if (t == 0) {
-        int run = 0;
-        for (int h = HEAT_BINS - 1; h >= 0; --h) {
-            const int c = bin[h];
-            bin[h] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    for (int i = t; i < n; i += blockDim.x) order[atomicAdd(&bin[min(heat[i], HEAT_BINS - 1)], 1)] = i;
-}
+
 
 template <typename T>
 __device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, int maxit) {
@@ -184,6 +161,8 @@ __device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, 
     a.tol = tol;
     a.ovf_list = nullptr;
     a.ovf_count = nullptr;
+    a.order = nullptr;
+    a.n_queue = f.p;
     return a;
 }
 
@@ -394,7 +373,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
         (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)b->total_cols, st)) != cudaSuccess)
         return e;
     batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits, lazy_order ? heat : nullptr);
-    if (lazy_order) batch_order_kernel<<<1, 1024, 0, st>>>(heat, b->total_cols, order);
+    if (lazy_order) order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, b->total_cols, order);
 
     const size_t budget = (size_t)max_smem_block() - 1024;
     const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;

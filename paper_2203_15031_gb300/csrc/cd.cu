@@ -74,7 +74,10 @@ __global__ void __launch_bounds__(512) cd_column_lazy_kernel(CDArgs<T> a) {
     ColCounters cnt;
     for (;;) {
         int j = 0;
-        if (lane == 0) j = atomicAdd(&ctrl->next_col, 1);
+        if (lane == 0) {
+            const int q = atomicAdd(&ctrl->next_col, 1);
+            j = q >= a.n_queue ? a.p : (a.order ? a.order[q] : q);
+        }
         j = __shfl_sync(FULL_MASK, j, 0);
         if (j >= a.p) break;
         if (!solve_column_lazy<T, STD>(j, wsm, a, cnt) && lane == 0)
@@ -287,14 +290,19 @@ __global__ void prep_diag_kernel(const T* __restrict__ S, int p, int standardize
 }
 
 // One block per row of S^C (grid-stride over rows).
+// With heat: per column, the count of off-diagonal standardised entries above
+// heat_lam (see order_by_heat_kernel).
 template <typename T>
 __global__ void prep_matrix_kernel(const T* __restrict__ S, int p, int ldp, const double* cs,
                                    const float* csf, T* SC, T* GT, T* diag, int init_g,
-                                   FitCtrl* ctrl) {
+                                   FitCtrl* ctrl, T heat_lam, int* heat) {
     bool bad = false;
-    for (int r = blockIdx.x; r < p; r += gridDim.x)
+    for (int r = blockIdx.x; r < p; r += gridDim.x) {
+        int cnt = 0;
         bad |= standardize_row<T>(S, p, ldp, r, cs, csf, SC, init_g ? GT : nullptr, nullptr,
-                                  diag, threadIdx.x, blockDim.x);
+                                  diag, threadIdx.x, blockDim.x, heat_lam, heat ? &cnt : nullptr);
+        if (cnt) atomicAdd(&heat[r], cnt);
+    }
     if (bad) set_error(ctrl, DEV_ERR_NONFINITE);
 }
 
@@ -313,6 +321,28 @@ __global__ void theta_kernel(const T* __restrict__ BT, int p, int ldp,
                              FitCtrl* ctrl) {
     if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
     theta_pair<T>(BT, p, ldp, sigma, cs, Theta, sigma_out, ctrl, blockIdx.x);
+}
+
+// One regression r (spmesl_scaled_lasso): beta over the other columns in
+// order, in the original scale (b^o_k = b^C_k c_k / c_r, proof of
+// Proposition 1), sigma^o = sigma^C / c_r, nonzero coefficients counted.
+template <typename T>
+__global__ void lasso_export_kernel(const T* __restrict__ BT, int p, int ldp, int r,
+                                    const double* __restrict__ sigma,
+                                    const double* __restrict__ cs, double* __restrict__ beta,
+                                    double* __restrict__ sigma_out, FitCtrl* ctrl) {
+    if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const T* brow = BT + (size_t)r * ldp;
+    bool nz = false;
+    if (k < p && k != r) {
+        const T b = brow[k];
+        nz = b != T(0);
+        beta[k < r ? k : k - 1] = (double)b * cs[k] / cs[r];
+    }
+    const unsigned cnt = __popc(__ballot_sync(FULL_MASK, nz));
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&ctrl->nnz, (unsigned long long)cnt);
+    if (k == 0) sigma_out[0] = sigma[r] / cs[r];
 }
 
 // B[j][k] = b_jk in the original scale: b^o_jk = b^C_jk c_j / c_k.
@@ -392,9 +422,37 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     a.tol = f.tol;
     a.ovf_list = a.flag;            // the column rule does not use the flag array
     a.ovf_count = &ctrl->ovf_count;
-    const bool joint = f.inner_rule == SPMESL_INNER_JOINT;
+    a.order = nullptr;
+    a.n_queue = f.p;
+    const bool single = f.response_col >= 0;    // one regression: lazy column rule
+    const bool joint = !single && f.inner_rule == SPMESL_INNER_JOINT;
+    // Lazy launch shape (warps per block, blocks per SM).
+    const bool lazy = single || (!joint && f.gradient != SPMESL_GRADIENT_EAGER);
+    auto lk = cd_column_lazy_kernel<T, STD>;
+    const size_t lper = lazy_warp_smem_bytes<T>(L.ldp);
+    int LW = f.warps_per_block > 0 ? f.warps_per_block : 8;
+    LW = std::max(1, std::min({LW, 16, (int)(smem_budget() / lper)}));
+    const size_t lsm = lper * LW;
+    int lper_sm = 1;
+    if (lazy) {
+        if ((e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lsm)) != cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper_sm, lk, 32 * LW, lsm)) !=
+            cudaSuccess)
+            return e;
+        lper_sm = std::max(lper_sm, 1);
+    }
+    // When there are more columns than resident warps, the lazy queue takes
+    // the columns heaviest first (standardised matrix).  The active index
+    // vectors are the joint rule's; the column rule lends them to the heat
+    // counts and the order.
+    const bool ordered = !single && lazy && f.standardize && f.p > g_num_sms * lper_sm * LW;
+    int* heat = ordered ? a.active_next : nullptr;
 
     if ((e = cudaMemsetAsync(ctrl, 0, sizeof(FitCtrl), st)) != cudaSuccess) return e;
+    if (ordered && (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)f.p, st)) != cudaSuccess)
+        return e;
     if ((e = cudaMemsetAsync(ws + L.BT, 0, (size_t)f.p * L.ldp * sizeof(T), st)) != cudaSuccess)
         return e;
     const int pb = 256;
@@ -406,7 +464,16 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
         prep_matrix_kernel<T><<<grid, pb, 0, st>>>(
             reinterpret_cast<const T*>(f.S), f.p, L.ldp, reinterpret_cast<double*>(ws + L.cs),
             reinterpret_cast<const float*>(ws + L.csf), reinterpret_cast<T*>(ws + L.SC), a.GT,
-            reinterpret_cast<T*>(ws + L.diag), joint ? 1 : 0, ctrl);
+            reinterpret_cast<T*>(ws + L.diag), joint ? 1 : 0, ctrl, (T)f.lambda0, heat);
+    }
+    if (ordered) {
+        order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, f.p, a.active);
+        a.order = a.active;
+    }
+    if (single) {
+        // a queue of one column: active[j] = j after prep_diag_kernel
+        a.order = a.active + f.response_col;
+        a.n_queue = 1;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
@@ -427,24 +494,14 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
 
     if (f.phase_events) cudaEventRecord(f.phase_events[0], st);
     if (!joint) {
-        const bool lazy = f.gradient != SPMESL_GRADIENT_EAGER;
         if (lazy) {
             // lazy gradient: small shared-memory footprint, many columns per SM
-            auto lk = cd_column_lazy_kernel<T, STD>;
-            const size_t lper = lazy_warp_smem_bytes<T>(L.ldp);
-            int LW = f.warps_per_block > 0 ? f.warps_per_block : 8;
-            LW = std::max(1, std::min({LW, 16, (int)(smem_budget() / lper)}));
-            const size_t lsm = lper * LW;
-            if ((e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)lsm)) != cudaSuccess)
-                return e;
-            int lper_sm = 0;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper_sm, lk, 32 * LW, lsm)) !=
-                cudaSuccess)
-                return e;
-            lper_sm = std::max(lper_sm, 1);
-            const int lgrid = std::min((f.p + LW - 1) / LW, g_num_sms * lper_sm);
-            lk<<<lgrid, 32 * LW, lsm, st>>>(a);
+            if (single) {
+                lk<<<1, 32, lper, st>>>(a);          // one warp for the one column
+            } else {
+                const int lgrid = std::min((f.p + LW - 1) / LW, g_num_sms * lper_sm);
+                lk<<<lgrid, 32 * LW, lsm, st>>>(a);
+            }
         }
         // eager gradient: all columns, or only those the lazy solver handed over
         auto kern = cd_column_kernel<T, STD>;
@@ -477,6 +534,13 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (f.phase_events) cudaEventRecord(f.phase_events[1], st);
 
+    if (single) {
+        lasso_export_kernel<T><<<(f.p + 255) / 256, 256, 0, st>>>(
+            a.BT, f.p, L.ldp, f.response_col, a.sigma, reinterpret_cast<const double*>(ws + L.cs),
+            f.beta_out, f.sigma_out, ctrl);
+        if (f.phase_events) cudaEventRecord(f.phase_events[2], st);
+        return cudaGetLastError();
+    }
     theta_kernel<T><<<theta_pairs<T>(f.p), dim3(32, 8), 0, st>>>(a.BT, f.p, L.ldp, a.sigma,
                                        reinterpret_cast<const double*>(ws + L.cs), f.Theta,
                                        f.sigma_out, ctrl);

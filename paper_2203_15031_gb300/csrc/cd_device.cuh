@@ -24,7 +24,37 @@ struct CDArgs {
     double lambda0, tol;
     int* ovf_list;       // columns handed from the lazy solver to the eager one
     int* ovf_count;
+    const int* order;    // queue order of the lazy solver (nullptr: 0..p-1)
+    int n_queue;         // columns the lazy solver takes from its queue
 };
+
+namespace {
+// Order of a coordinate-descent queue: columns by decreasing heat (the count
+// of off-diagonal standardised entries above lambda0, from standardize_row;
+// counting sort, one block), so the longest column solves start first instead
+// of in the tail of the launch.  Ties in any order: a column's result does not
+// depend on when it runs.
+constexpr int HEAT_BINS = 64;
+__global__ void __launch_bounds__(1024) order_by_heat_kernel(const int* __restrict__ heat, int n,
+                                                          int* __restrict__ order) {
+    __shared__ int bin[HEAT_BINS];
+    const int t = threadIdx.x;
+    if (t < HEAT_BINS) bin[t] = 0;
+    __syncthreads();
+    for (int i = t; i < n; i += blockDim.x) atomicAdd(&bin[min(heat[i], HEAT_BINS - 1)], 1);
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int h = HEAT_BINS - 1; h >= 0; --h) {
+            const int c = bin[h];
+            bin[h] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < n; i += blockDim.x) order[atomicAdd(&bin[min(heat[i], HEAT_BINS - 1)], 1)] = i;
+}
+}  // namespace
 
 template <typename T>
 __device__ __forceinline__ T soft(T x, T lam) {

@@ -115,6 +115,11 @@ struct FitLaunch {
     unsigned char* ws;   // workspace base
     cudaEvent_t* phase_events;   // nullptr, or 3 events: before CD, after CD, after Theta
     int gradient;                // spmesl_gradient (column rule only)
+    // >= 0: solve only this column (one scaled-lasso regression, lazy column
+    // rule) and write its coefficients to beta_out (the p - 1 other columns in
+    // order, original scale) and its sigma to sigma_out[0] instead of Theta
+    int response_col = -1;
+    double* beta_out = nullptr;
 };
 cudaError_t launch_fit(const FitLaunch& f, cudaStream_t st);
 cudaError_t launch_export_B(const unsigned char* ws, int p, int precision, double* B,

@@ -136,6 +136,33 @@ def make_problem(kind: str, p: int, n: int, seed: int, dtype=np.float32) -> Prob
     return Problem(kind, p, n, seed, dtype, theta, X)
 
 
+class Regression:
+    """One scaled-lasso regression problem: predictors X (n x p, rows drawn
+    from N(0, Theta^-1) of the given network), y = X beta_true + noise * z."""
+
+    def __init__(self, kind, p, n, seed, dtype, X, y, beta_true, noise):
+        self.kind, self.p, self.n, self.seed, self.dtype = kind, p, n, seed, dtype
+        self.X, self.y, self.beta_true, self.noise = X, y, beta_true, noise
+
+    @property
+    def lambda0(self) -> float:
+        return math.sqrt(2.0 * math.log(self.p) / self.n)
+
+
+def make_regression(kind: str, p: int, n: int, seed: int, k: int = 10, noise: float = 0.5,
+                    dtype=np.float32) -> Regression:
+    """k nonzero coefficients +-1 at random positions; y = X beta + noise z.
+    y is formed in FP64 from the stored (dtype) X, then stored as dtype."""
+    rng = np.random.default_rng(seed)
+    theta = make_theta(kind, p, rng)
+    X = sample_x(theta, n, rng, dtype=dtype)
+    beta = np.zeros(p)
+    idx = rng.choice(p, min(k, p), replace=False)
+    beta[idx] = rng.choice([-1.0, 1.0], idx.size)
+    y = (X.astype(np.float64) @ beta + noise * rng.standard_normal(n)).astype(dtype)
+    return Regression(kind, p, n, seed, dtype, X, y, beta, noise)
+
+
 # Workloads, named by what they are.
 WORKLOADS = {
     # AR(1) p=100 n=50, FP64 end to end, tol 1e-8, maxit 1000
@@ -148,6 +175,11 @@ WORKLOADS = {
     "hub_p10000_n500_mixed": dict(kind="hub", p=10000, n=500, dtype=np.float32, tol=1e-6,
                                   maxit=1000, prec="mixed"),
 }
+
+# One scaled-lasso regression (spmesl_scaled_lasso): Erdos-Renyi predictors
+# p=2000, n=200, 10 active coefficients, noise 0.5, split-BF16 Gram of [X y].
+REGRESSION = dict(kind="er", p=2000, n=200, k=10, noise=0.5, dtype=np.float32, tol=1e-6,
+                  maxit=1000, prec="mixed")
 
 
 def batch_specs(count: int = 256, seed: int = 1000, p_lo: int = 50, p_hi: int = 2000,
