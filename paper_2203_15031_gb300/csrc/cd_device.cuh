@@ -510,7 +510,11 @@ __device__ void solve_column(int j, T* __restrict__ g, T* __restrict__ b, int* _
 // If the support outgrows the list, the column is handed to the eager solver
 // (solve_column) through a queue and solved again from the start.
 // ===========================================================================
-constexpr int LAZY_CAP = 512;
+constexpr int LAZY_CAP = 256;
+
+// Supports up to ACT_MAX coordinates get the active-set phase (one
+// coordinate per lane, the support's block of S in shared memory).
+constexpr int ACT_MAX = 32;
 
 template <typename T>
 struct Support {
@@ -521,7 +525,8 @@ struct Support {
 
 template <typename T>
 __host__ __device__ constexpr size_t lazy_warp_smem_bytes(int ldp) {
-    return (size_t)LAZY_CAP * (sizeof(int) + sizeof(T)) + (size_t)num_chunks(ldp) * sizeof(ChunkInfo);
+    return (size_t)LAZY_CAP * (sizeof(int) + sizeof(T)) + (size_t)num_chunks(ldp) * sizeof(ChunkInfo) +
+           (size_t)ACT_MAX * ACT_MAX * sizeof(T);
 }
 
 // Set b_k = v in the sorted support (insert, update or remove).  pos is the
@@ -729,6 +734,73 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
     return maxd;
 }
 
+// Active-set phase of the lasso at a fixed lambda: cyclic sweeps (ascending
+// coordinate order) over the current support A only, until a sweep moves no
+// coefficient by tol or more (at most maxit sweeps).  Lane m holds coordinate
+// A_m: its b and g_m = S_jm - sum_{l in A} S_ml b_l; the block S_AA is
+// gathered once into shared memory (column k at saa + k ACT_MAX).  Every move
+// is added to the column's running sums, so the chunk skip test stays exact
+// for the coordinates outside A.  Coordinates that reach zero leave the
+// support.  Returns the sweeps done (0 when A is empty or larger than ACT_MAX).
+template <typename T, bool STD>
+__device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* __restrict__ saa,
+                            unsigned long long& moves, ColScan& cs) {
+    const int lane = threadIdx.x & 31;
+    const int n = s.n;
+    if (n == 0 || n > ACT_MAX) return 0;
+    const int ldp = a.ldp;
+#pragma unroll 8
+    for (int t = lane; t < n * n; t += 32) {
+        const int k = t / n, m = t - k * n;
+        saa[k * ACT_MAX + m] = a.SC[(size_t)s.idx[m] * ldp + s.idx[k]];
+    }
+    const int my = lane < n ? s.idx[lane] : 0;
+    T b = lane < n ? s.val[lane] : T(0);
+    T g = lane < n ? a.SC[(size_t)j * ldp + my] : T(0);
+    T skk = T(1);
+    if constexpr (!STD) skk = lane < n ? a.diag[my] : T(1);
+    __syncwarp();
+    for (int l = 0; l < n; ++l) {
+        const T bl = __shfl_sync(FULL_MASK, b, l);
+        if (lane < n) g = fma(-saa[l * ACT_MAX + lane], bl, g);
+    }
+    int sw = 0;
+    while (sw < a.maxit) {
+        ++sw;
+        T md = T(0);
+        for (int k = 0; k < n; ++k) {
+            T nb = b, d = T(0);
+            if (lane == k) {
+                if constexpr (STD) nb = soft<T>(g + b, lam);                 // S_kk = 1
+                else nb = soft<T>(g + skk * b, lam) / skk;
+                d = nb - b;
+            }
+            d = __shfl_sync(FULL_MASK, d, k);
+            if (d != T(0)) {
+                if (lane < n) g = fma(-saa[k * ACT_MAX + lane], d, g);
+                if (lane == k) b = nb;
+                md = fmax(md, fabs(d));
+                ++moves;
+                cs.dsum += fabsf((float)d);
+                ++cs.nmoves;
+            }
+        }
+        if ((double)md < a.tol) break;
+    }
+    // write back, dropping coordinates at zero (the list stays sorted)
+    const bool keep = lane < n && b != T(0);
+    const unsigned km = __ballot_sync(FULL_MASK, keep);
+    const int pos = __popc(km & ((1u << lane) - 1u));
+    __syncwarp();
+    if (keep) {
+        s.idx[pos] = my;
+        s.val[pos] = b;
+    }
+    s.n = __popc(km);
+    __syncwarp();
+    return sw;
+}
+
 // sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the sorted support (Eq. (14)).
 template <typename T>
 __device__ double residual_quadratic_form_list(int j, const Support<T>& s, const CDArgs<T>& a) {
@@ -761,6 +833,7 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
     s.val = reinterpret_cast<T*>(wsm + LAZY_CAP * sizeof(int));
     s.n = 0;
     ColScan cs{reinterpret_cast<ChunkInfo*>(wsm + LAZY_CAP * (sizeof(int) + sizeof(T))), 0.f, 0u};
+    T* saa = reinterpret_cast<T*>(cs.ci + num_chunks(a.ldp));
     reset_chunks(cs, a.ldp);
     __syncwarp();
 
@@ -774,6 +847,9 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
         const T lam = (T)(sigma * a.lambda0);
         bool inner_ok = false;
         for (int m = 0; m < a.maxit; ++m) {
+            // converge on the support first, then a full sweep decides (the
+            // stop rule of Algorithm 1: a full sweep with max |delta| < tol)
+            cnt.sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.moves, cs);
             const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow);
             ++cnt.sweeps;
             if (overflow) return false;
