@@ -252,7 +252,7 @@ def run_ours(args):
             raise RuntimeError(f"warm-up fits did not converge: {statuses}")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        cd_ms, moves, sweeps, nnzb = [], [], [], []
+        cd_ms, moves, sweeps, nnzb, act = [], [], [], [], []
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -268,6 +268,7 @@ def run_ours(args):
             moves.append(st["moves"])
             sweeps.append(st["inner_sweeps"])
             nnzb.append(st["nnz_B"])
+            act.append((st["active_sweeps"], st["active_moves"]))
         torch.cuda.synchronize()
         if sampler:
             sampler.__exit__(None, None, None)
@@ -279,12 +280,12 @@ def run_ours(args):
             t = torch.tensor([total_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
-        return bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb
+        return bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb, act
 
     clk = ClockSampler(local_rank)
-    bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb = batched(BATCH_PREC, clk)   # headline
+    bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb, act = batched(BATCH_PREC, clk)
     value = world * N_DATASETS * args.steps / (total_ms / 1e3)
-    bt32, _, per32, total32, _, _, _, _ = batched("fp32")
+    bt32, _, per32, total32, _, _, _, _, _ = batched("fp32")
     value32 = world * N_DATASETS * args.steps / (total32 / 1e3)
     bt32.close()
 
@@ -358,10 +359,11 @@ def run_ours(args):
 
     if rank == 0:
         hbm, which = _peaks()
-        # algorithmic bytes of one batched CD launch: every column loads S_.j
-        # into shared memory and writes b_j back (2 p rows of ldp floats per
-        # fit), and every coordinate move reads one S row (the column slice
-        # of the rank-1 update).
+        # algorithmic bytes of one batched CD launch: every column reads S_.j
+        # and writes b_j (2 p rows of ldp floats per fit), and every move of a
+        # full sweep reads one S row (the column slice of the rank-1 update);
+        # moves of the active-set phase read the support's block of S, held
+        # in shared memory, and are counted apart
         ldp = (p + 31) // 32 * 32
         mv = statistics.mean(moves)
         bytes_cd = 4.0 * ldp * (2 * p * N_DATASETS + mv)
@@ -373,6 +375,8 @@ def run_ours(args):
                 "kernel": "batch_cd_lazy_kernel<float,1>", "peak_kind": which,
                 "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cd_mean_ms,
                 "moves_per_launch": mv, "warps_per_block": best_w,
+                "active_sweeps_per_launch": statistics.mean(a for a, _ in act),
+                "active_moves_per_launch": statistics.mean(m for _, m in act),
                 "sweep_model": sweep_model(4, p, statistics.mean(sweeps), mv,
                                            statistics.mean(nnzb), cd_mean_ms, hbm)}
         srt = sorted(per)
@@ -466,7 +470,7 @@ def run_single(args):
     st = sp.Stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    gram_ms, cd_ms, moves, sweeps, nnzb = [], [], [], [], []
+    gram_ms, cd_ms, moves, sweeps, nnzb, act_s, act_m = [], [], [], [], [], [], []
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         for i in range(args.steps):
@@ -480,6 +484,8 @@ def run_single(args):
             moves.append(st.moves)
             sweeps.append(st.inner_sweeps)
             nnzb.append(st.nnz_B)
+            act_s.append(st.active_sweeps)
+            act_m.append(st.active_moves)
         torch.cuda.synchronize()
     per = [a.elapsed_time(b) for a, b in ev]
     value = args.steps / (sum(per) / 1e3)
@@ -493,6 +499,8 @@ def run_single(args):
             "frac": bytes_cd / (cdm / 1e3) / 1e9 / hbm, "traffic": None,
             "kernel": "cd_column_lazy_kernel", "peak_kind": which,
             "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cdm, "moves_per_launch": mv,
+            "active_sweeps_per_launch": statistics.mean(act_s),
+            "active_moves_per_launch": statistics.mean(act_m),
             "sweep_model": sweep_model(s, p, statistics.mean(sweeps), mv, statistics.mean(nnzb),
                                        cdm, hbm)}
     gm = statistics.mean(gram_ms)

@@ -122,6 +122,9 @@ typedef struct {
     float ms_total;             /* serving: submit -> completion seen by the context, ms */
     int32_t batch_size;         /* serving: requests in the batch this one ran in */
     int32_t reserved32;
+    int64_t active_sweeps;      /* sum over columns of sweeps over the support only (lazy solver) */
+    int64_t active_moves;       /* coordinate updates in those sweeps (no S-row read: the support's
+                                   block of S is held in shared memory) */
 } spmesl_stats;
 
 /* Fill `opts` with the defaults: FP32, standardize = 1, center = 0,

@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("ms_theta", ctypes.c_float), ("max_col_sweeps", ctypes.c_int32),
                 ("max_col_outer", ctypes.c_int32), ("ms_queue", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("batch_size", ctypes.c_int32),
-                ("reserved32", ctypes.c_int32)]
+                ("reserved32", ctypes.c_int32), ("active_sweeps", ctypes.c_int64),
+                ("active_moves", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}

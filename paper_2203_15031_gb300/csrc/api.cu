@@ -357,6 +357,8 @@ spmesl_status spmesl_fit_result(const void* workspace, int p, int precision, spm
         stats->outer_iters = c.outer_max;
         stats->inner_sweeps = (int64_t)c.total_sweeps;
         stats->moves = (int64_t)c.moves;
+        stats->active_sweeps = (int64_t)c.act_sweeps;
+        stats->active_moves = (int64_t)c.act_moves;
         stats->nnz_B = (int64_t)c.nnz;
         stats->n_not_converged = c.n_not_converged;
         stats->n_degenerate = c.n_degenerate;

@@ -725,6 +725,8 @@ spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, 
         agg.outer_iters = std::max(agg.outer_iters, c.outer_max);
         agg.inner_sweeps += (int64_t)c.total_sweeps;
         agg.moves += (int64_t)c.moves;
+        agg.active_sweeps += (int64_t)c.act_sweeps;
+        agg.active_moves += (int64_t)c.act_moves;
         agg.nnz_B += (int64_t)c.nnz;
         agg.n_not_converged += c.n_not_converged;
         agg.n_degenerate += c.n_degenerate;

@@ -420,7 +420,8 @@ __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, 
 
 // Per-warp counters of the column solves, flushed into a fit's FitCtrl.
 struct ColCounters {
-    unsigned long long sweeps = 0, moves = 0;
+    unsigned long long sweeps = 0, moves = 0;        // full sweeps and their moves
+    unsigned long long act_sweeps = 0, act_moves = 0;   // active-set phase
     int outer_max = 0, n_nc = 0, n_deg = 0, max_sw = 0;
 };
 
@@ -428,6 +429,8 @@ __device__ __forceinline__ void flush_counters(FitCtrl* ctrl, ColCounters& c) {
     if ((threadIdx.x & 31) == 0) {
         if (c.sweeps) atomicAdd(&ctrl->total_sweeps, c.sweeps);
         if (c.moves) atomicAdd(&ctrl->moves, c.moves);
+        if (c.act_sweeps) atomicAdd(&ctrl->act_sweeps, c.act_sweeps);
+        if (c.act_moves) atomicAdd(&ctrl->act_moves, c.act_moves);
         atomicMax(&ctrl->outer_max, c.outer_max);
         atomicMax(&ctrl->max_col_sweeps, c.max_sw);
         if (c.n_nc) atomicAdd(&ctrl->n_not_converged, c.n_nc);
@@ -849,7 +852,7 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
         for (int m = 0; m < a.maxit; ++m) {
             // converge on the support first, then a full sweep decides (the
             // stop rule of Algorithm 1: a full sweep with max |delta| < tol)
-            cnt.sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.moves, cs);
+            cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.act_moves, cs);
             const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow);
             ++cnt.sweeps;
             if (overflow) return false;

@@ -42,6 +42,8 @@ struct FitCtrl {
     int ovf_count;                     // columns handed from the lazy to the eager solver
     int ovf_next;                      // eager solver's position in that queue
     int pad[4];
+    unsigned long long act_sweeps;     // lazy solver: sweeps over the support only
+    unsigned long long act_moves;      // moves in those sweeps
 };
 static_assert(sizeof(FitCtrl) <= 256, "FitCtrl must fit its 256-byte slot");
 
