@@ -45,9 +45,9 @@ N_DATASETS = 10
 # sigma / convergence / Theta in FP64
 BATCH_PREC = "mixed"
 # per batched step: split/transpose, tcgen05 Gram, prep_diag, prep_matrix, column
-# order, lazy cd, eager cd queue, theta (the FP32 path has one SIMT Gram launch
-# instead of two)
-KERNELS_PER_SOLVE = {"mixed": 8, "fp32": 7}
+# order, lazy cd, eager cd queue, Theta zeroing (side stream), theta (the FP32
+# path has one SIMT Gram launch instead of two)
+KERNELS_PER_SOLVE = {"mixed": 9, "fp32": 8}
 
 
 def _env_rank():

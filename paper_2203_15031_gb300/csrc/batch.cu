@@ -240,6 +240,25 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
     }
 }
 
+// Zero every fit's Theta (16-byte stores where aligned).  It runs on a side
+// stream under the coordinate-descent launch, which leaves HBM idle; the
+// Theta kernel then writes only the nonzero entries.
+__global__ void batch_zero_theta_kernel(const BatchFit* __restrict__ fits, int count) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int fi = 0; fi < count; ++fi) {
+        double* th = fits[fi].Theta;
+        const size_t n = (size_t)fits[fi].p * fits[fi].p;
+        if ((reinterpret_cast<uintptr_t>(th) & 15) == 0) {
+            double2* t2 = reinterpret_cast<double2*>(th);
+            for (size_t i = tid; i < n / 2; i += stride) t2[i] = make_double2(0.0, 0.0);
+            if ((n & 1) && tid == 0) th[n - 1] = 0.0;
+        } else {
+            for (size_t i = tid; i < n; i += stride) th[i] = 0.0;
+        }
+    }
+}
+
 template <typename T>
 __global__ void batch_theta_kernel(const BatchFit* __restrict__ fits,
                                    const int* __restrict__ theta_prefix, int count) {
@@ -323,6 +342,9 @@ struct spmesl_batch {
     const void* graph_ws = nullptr;
     int graph_W = -1;
     cudaStream_t cap_stream = nullptr;
+    // side stream that zeroes Theta under the coordinate-descent launch
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     // record_phase_times (runs without a graph): events around the CD launch
     int record_phase_times = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -347,6 +369,12 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     if ((e = cudaMemsetAsync(ws + b->off_ctrls, 0, (size_t)256 * b->count, st)) != cudaSuccess)
         return e;
     const int count = b->count;
+    // fork: Theta is zeroed on the side stream while the fits run
+    if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->side, b->fork, 0)) != cudaSuccess)
+        return e;
+    batch_zero_theta_kernel<<<num_sms() * 4, 256, 0, b->side>>>(fits, count);
+    if ((e = cudaEventRecord(b->join, b->side)) != cudaSuccess) return e;
     if (b->any_x) {
         if (b->center)
             batch_mean_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits);
@@ -418,6 +446,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     kern<<<grid, 32 * EW, smem, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
                                       b->maxit, hdr, ovf, lazy ? 1 : 0);
     if (timed) cudaEventRecord(b->ev[1], st);
+    if ((e = cudaStreamWaitEvent(st, b->join, 0)) != cudaSuccess) return e;   // join
     batch_theta_kernel<T><<<b->total_theta, dim3(32, 8), 0, st>>>(fits, thetap, count);
     return cudaGetLastError();
 }
@@ -661,6 +690,12 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
         }
     }
     const int W = b->warps_per_block > 0 ? b->warps_per_block : auto_warps(b);
+    if (!b->side) {
+        if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+            return SPMESL_ECUDA;
+    }
     auto enqueue = [&](cudaStream_t s2) {
         return b->precision == SPMESL_FP64 ? enqueue_batch<double>(b, ws, s2, W)
                                            : enqueue_batch<float>(b, ws, s2, W);
@@ -789,6 +824,9 @@ void spmesl_batch_destroy(spmesl_batch* b) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
     if (b->ev[1]) cudaEventDestroy(b->ev[1]);
     if (b->pinned) {

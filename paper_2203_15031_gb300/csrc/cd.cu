@@ -323,6 +323,20 @@ __global__ void theta_kernel(const T* __restrict__ BT, int p, int ldp,
     theta_pair<T>(BT, p, ldp, sigma, cs, Theta, sigma_out, ctrl, blockIdx.x);
 }
 
+// Zero n doubles (16-byte stores where aligned): Theta before the sparse
+// Theta kernel.
+__global__ void zero_kernel(double* __restrict__ x, size_t n) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        double2* x2 = reinterpret_cast<double2*>(x);
+        for (size_t i = tid; i < n / 2; i += stride) x2[i] = make_double2(0.0, 0.0);
+        if ((n & 1) && tid == 0) x[n - 1] = 0.0;
+    } else {
+        for (size_t i = tid; i < n; i += stride) x[i] = 0.0;
+    }
+}
+
 // One regression r (spmesl_scaled_lasso): beta over the other columns in
 // order, in the original scale (b^o_k = b^C_k c_k / c_r, proof of
 // Proposition 1), sigma^o = sigma^C / c_r, nonzero coefficients counted.
@@ -541,6 +555,7 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
         if (f.phase_events) cudaEventRecord(f.phase_events[2], st);
         return cudaGetLastError();
     }
+    zero_kernel<<<g_num_sms * 4, 256, 0, st>>>(f.Theta, (size_t)f.p * f.p);
     theta_kernel<T><<<theta_pairs<T>(f.p), dim3(32, 8), 0, st>>>(a.BT, f.p, L.ldp, a.sigma,
                                        reinterpret_cast<const double*>(ws + L.cs), f.Theta,
                                        f.sigma_out, ctrl);

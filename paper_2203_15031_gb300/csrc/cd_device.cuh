@@ -895,9 +895,10 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
 // tile of rows j0.., columns k0.. (j0 <= k0) and its mirror.  Omega_1 = -B D
 // on the working scale, min-magnitude symmetrisation (for j < k a tie keeps
 // omega_jk) and Omega^o = C Omega C.  Both coefficient tiles are read once
-// into shared memory; one pass writes the tile and a second its mirror, each
-// with rows of TS consecutive doubles.  Every value is computed from the same
-// (j, k) in both passes, so Theta is exactly symmetric.  Blocks of the first
+// into shared memory.  Theta must be zero on entry (the launchers clear it
+// with a memset, a pure streaming write): only the diagonal and the pairs
+// with a nonzero coefficient are written, both entries of a pair with the
+// same value, so Theta is exactly symmetric.  Blocks of the first
 // tile row also write sigma in the original scale; nonzero coefficients are
 // counted into ctrl->nnz.  Block shape 32 x 8.  TS = 64 for FP32
 // coefficients, 32 for FP64 (static shared memory).
@@ -978,48 +979,23 @@ __device__ void theta_pair(const T* __restrict__ BT, int p, int ldp,
         else out = fabs(okj) > fabs(ojk) ? ojk : okj;  // pair (k, j) with k < j
         return out * (c_j[jj] * c_k[kk]);
     };
+    // Theta is zeroed before the launch: only the diagonal and the pairs with
+    // a nonzero coefficient are written, each pair's two entries by the same
+    // thread (on the diagonal tile both orders of a pair are visited and
+    // write the same value)
     unsigned long long nnz = 0;
-    if (TS == 64 && (p & 1) == 0 && (reinterpret_cast<uintptr_t>(Theta) & 15) == 0) {
-        // two consecutive entries per lane, 16-byte stores: a warp writes 64
-        // entries of a row (p even: p - 1 is odd, so an entry pair never
-        // straddles p)
-        const int e = 2 * tx;
-        for (int jj = ty; jj < TS; jj += 8) {              // the tile: rows j
-            const int j = j0 + jj, k = k0 + e;
+    for (int jj = ty; jj < TS; jj += 8)
+        for (int kk = tx; kk < TS; kk += 32) {
+            const int j = j0 + jj, k = k0 + kk;
             if (j >= p || k >= p) continue;
-            nnz += (j != k && tB[jj][e] != T(0)) + (j != k + 1 && tB[jj][e + 1] != T(0));
-            *reinterpret_cast<double2*>(Theta + (size_t)j * p + k) =
-                make_double2(value(jj, e), value(jj, e + 1));
-        }
-        if (j0 != k0) {
-            for (int kk = ty; kk < TS; kk += 8) {          // the mirror: rows k
-                const int j = j0 + e, k = k0 + kk;
-                if (j >= p || k >= p) continue;
-                nnz += (tA[kk][e] != T(0)) + (tA[kk][e + 1] != T(0));
-                *reinterpret_cast<double2*>(Theta + (size_t)k * p + j) =
-                    make_double2(value(e, kk), value(e + 1, kk));
+            const bool nz_kj = tB[jj][kk] != T(0), nz_jk = tA[kk][jj] != T(0);
+            nnz += (j != k && nz_kj) + (j0 != k0 && nz_jk);
+            if (j == k || nz_kj || nz_jk) {
+                const double v = value(jj, kk);
+                Theta[(size_t)j * p + k] = v;
+                Theta[(size_t)k * p + j] = v;
             }
         }
-    } else {
-        // the tile: rows j, lanes along k
-        for (int jj = ty; jj < TS; jj += 8)
-            for (int kk = tx; kk < TS; kk += 32) {
-                const int j = j0 + jj, k = k0 + kk;
-                if (j >= p || k >= p) continue;
-                nnz += (j != k && tB[jj][kk] != T(0));
-                Theta[(size_t)j * p + k] = value(jj, kk);
-            }
-        // the mirror: rows k, lanes along j
-        if (j0 != k0) {
-            for (int kk = ty; kk < TS; kk += 8)
-                for (int jj = tx; jj < TS; jj += 32) {
-                    const int j = j0 + jj, k = k0 + kk;
-                    if (j >= p || k >= p) continue;
-                    nnz += (tA[kk][jj] != T(0));
-                    Theta[(size_t)k * p + j] = value(jj, kk);
-                }
-        }
-    }
     if (j0 == 0 && lin < TS && k0 + lin < p) sigma_out[k0 + lin] = sigma[k0 + lin] / cs[k0 + lin];
     // one atomic per warp
 #pragma unroll
