@@ -122,7 +122,7 @@ __global__ void batch_prep_diag_kernel(const BatchFit* __restrict__ fits, int st
 }
 
 // blockIdx.y = fit; blocks stride over the fit's rows (same arithmetic as
-// the single-fit prep_matrix_kernel), clearing BT on the way.  With heat,
+// the single-fit prep_matrix_kernel; BT is cleared on the side stream).  With heat,
 // also counts per column the off-diagonal entries of the standardised matrix
 // above lambda0: the coordinates that can move in the column's first sweep,
 // a predictor of how long the column takes.
@@ -133,7 +133,7 @@ __global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits, int*
     for (int r = blockIdx.x; r < f.p; r += gridDim.x) {
         int cnt = 0;
         bad |= standardize_row<T>(static_cast<const T*>(f.S), f.p, f.ldp, r, f.cs, f.csf,
-                                  static_cast<T*>(f.SC), nullptr, static_cast<T*>(f.BT),
+                                  static_cast<T*>(f.SC), nullptr, nullptr,
                                   static_cast<T*>(f.diag), threadIdx.x, blockDim.x,
                                   (T)f.lambda0, heat ? &cnt : nullptr);
         if (cnt) atomicAdd(&heat[f.col_start + r], cnt);
@@ -240,22 +240,30 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
     }
 }
 
-// Zero every fit's Theta (16-byte stores where aligned).  It runs on a side
-// stream under the coordinate-descent launch, which leaves HBM idle; the
-// Theta kernel then writes only the nonzero entries.
-__global__ void batch_zero_theta_kernel(const BatchFit* __restrict__ fits, int count) {
+// Zero every fit's Theta (what = 0) or coefficient rows BT (what = 1;
+// elem bytes per element), with 16-byte stores where aligned.  Both run on
+// a side stream: BT under the Gram and the standardisation (the
+// coordinate-descent launch waits for it), Theta under the
+// coordinate-descent launch, which leaves HBM idle.  The Theta kernel then
+// writes only the nonzero entries.
+__global__ void batch_zero_kernel(const BatchFit* __restrict__ fits, int count, int what,
+                                  int elem) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (int fi = 0; fi < count; ++fi) {
-        double* th = fits[fi].Theta;
-        const size_t n = (size_t)fits[fi].p * fits[fi].p;
-        if ((reinterpret_cast<uintptr_t>(th) & 15) == 0) {
-            double2* t2 = reinterpret_cast<double2*>(th);
-            for (size_t i = tid; i < n / 2; i += stride) t2[i] = make_double2(0.0, 0.0);
-            if ((n & 1) && tid == 0) th[n - 1] = 0.0;
-        } else {
-            for (size_t i = tid; i < n; i += stride) th[i] = 0.0;
-        }
+        const BatchFit& f = fits[fi];
+        unsigned char* base = what == 0 ? reinterpret_cast<unsigned char*>(f.Theta)
+                                        : static_cast<unsigned char*>(f.BT);
+        const size_t bytes = what == 0 ? sizeof(double) * (size_t)f.p * f.p
+                                       : (size_t)elem * f.p * f.ldp;
+        const size_t head = (16 - (reinterpret_cast<uintptr_t>(base) & 15)) & 15;
+        const size_t h = head < bytes ? head : bytes;
+        if (tid < h) base[tid] = 0;
+        float4* q = reinterpret_cast<float4*>(base + h);
+        const size_t nq = (bytes - h) / 16;
+        for (size_t i = tid; i < nq; i += stride) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const size_t tail = h + nq * 16;
+        if (tid < bytes - tail) base[tail + tid] = 0;
     }
 }
 
@@ -344,7 +352,7 @@ struct spmesl_batch {
     cudaStream_t cap_stream = nullptr;
     // side stream that zeroes Theta under the coordinate-descent launch
     cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, join_bt = nullptr;
     // record_phase_times (runs without a graph): events around the CD launch
     int record_phase_times = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -373,7 +381,9 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(b->side, b->fork, 0)) != cudaSuccess)
         return e;
-    batch_zero_theta_kernel<<<num_sms() * 4, 256, 0, b->side>>>(fits, count);
+    batch_zero_kernel<<<num_sms() * 4, 256, 0, b->side>>>(fits, count, 1, (int)sizeof(T));
+    if ((e = cudaEventRecord(b->join_bt, b->side)) != cudaSuccess) return e;
+    batch_zero_kernel<<<num_sms() * 4, 256, 0, b->side>>>(fits, count, 0, 8);
     if ((e = cudaEventRecord(b->join, b->side)) != cudaSuccess) return e;
     if (b->any_x) {
         if (b->center)
@@ -406,6 +416,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     const size_t budget = (size_t)max_smem_block() - 1024;
     const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
     int* ovf = reinterpret_cast<int*>(ws + b->off_ovf);
+    if ((e = cudaStreamWaitEvent(st, b->join_bt, 0)) != cudaSuccess) return e;   // BT is zero
     const bool timed = b->record_phase_times && b->ev[0];
     if (timed) cudaEventRecord(b->ev[0], st);
     if (lazy) {
@@ -693,7 +704,8 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
     if (!b->side) {
         if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join_bt, cudaEventDisableTiming) != cudaSuccess)
             return SPMESL_ECUDA;
     }
     auto enqueue = [&](cudaStream_t s2) {
@@ -827,6 +839,7 @@ void spmesl_batch_destroy(spmesl_batch* b) {
     if (b->side) cudaStreamDestroy(b->side);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
+    if (b->join_bt) cudaEventDestroy(b->join_bt);
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
     if (b->ev[1]) cudaEventDestroy(b->ev[1]);
     if (b->pinned) {
