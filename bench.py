@@ -670,6 +670,156 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch256(args):
+    """The 256-fit batch: p log-uniform in [50, 2000], n uniform in [30, 400],
+    networks AR(1) / Erdos-Renyi / hub at random (fit i: seed 1000 + i), one
+    CUDA-graph launch per step, mixed precision, warps per block autotuned;
+    against the plain path (one spmesl_gram + spmesl_fit per fit, FP32)."""
+    import numpy as np
+    import torch
+
+    import paper_2203_15031_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sp.lib()
+    specs = synth.batch_specs(256)
+    probs = [synth.make_problem(s["kind"], s["p"], s["n"], s["seed"], dtype=np.float32)
+             for s in specs]
+    inputs = [(torch.from_numpy(pr.X).to(dev), pr.lambda0) for pr in probs]
+    tol, maxit = 1e-6, 1000
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    bt = sp.Batch(inputs, kind="X", precision=BATCH_PREC, tol=tol, maxit=maxit, use_graph=True)
+    w = bt.tune()
+    for _ in range(args.warmup):
+        bt.run(stream)
+    statuses, _ = bt.result(stream)
+    if any(s not in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED) for s in statuses):
+        raise RuntimeError(f"warm-up batch failed: {statuses}")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            bt.run(stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    value = 256 * args.steps / (sum(per) / 1e3)
+    _, st = bt.result(stream)
+    # plain path over the same fits: one spmesl_gram + spmesl_fit per fit
+    # through the C ABI, buffers allocated beforehand, serialised on the stream
+    # (two passes, the second timed)
+    opts = sp.spmesl_default_opts()
+    opts.precision = sp.FP32
+    bufs = []
+    for (X, lam), pr in zip(inputs, probs):
+        p, n = pr.p, pr.n
+        gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
+        fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
+        bufs.append((X, lam, p, n, torch.empty((p, p), dtype=torch.float32, device=dev),
+                     torch.empty((p, p), dtype=torch.float64, device=dev),
+                     torch.empty(p, dtype=torch.float64, device=dev),
+                     sp._workspace(max(gnb, 1), dev), gnb, sp._workspace(fnb, dev), fnb))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rep in range(2):
+        e0.record(stream)
+        for X, lam, p, n, S, T, sg, (gk, gws), gnb, (fk, fws), fnb in bufs:
+            sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S, p, gws, gnb, stream), "gram")
+            sp._check(sp.spmesl_fit(S, n, p, lam, tol, maxit, opts, T, sg, None, fws, fnb,
+                                    stream), "fit")
+        e1.record(stream)
+        torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    del bufs
+    srt = sorted(per)
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(per) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch256", "fits_per_step": 256,
+                       "p": "log-uniform [50, 2000]", "n": "uniform [30, 400]",
+                       "networks": "ar1 / er / hub_scaled", "seeds": "1000-1255",
+                       "precision": BATCH_PREC, "graph": True, "warps_per_block": w,
+                       "tol": tol, "maxit": maxit, "l2": "flushed between steps (256 MB write)"},
+            "latency": {"p50_ms": statistics.median(per),
+                        "p99_ms": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]},
+            "plain": {"value": 256 / (plain_ms / 1e3), "unit": "solves/s", "precision": "fp32",
+                      "path": "one spmesl_gram + spmesl_fit per fit, serialised"},
+            "solve": {"moves": st["moves"], "full_sweeps": st["inner_sweeps"],
+                      "active_sweeps": st["active_sweeps"], "max_col_outer": st["max_col_outer"]},
+            "gpu_launches": KERNELS_PER_SOLVE[BATCH_PREC] * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    bt.close()
+
+
+# Table 4 of the paper (values as printed, with their standard errors): the
+# committed fixture tests/golden/table4_ar_p500_n250.json.
+TABLE4_FIXTURE = "tests/golden/table4_ar_p500_n250.json"
+TABLE4_KEYS = ["n_edges_hat", "sen", "spe", "fdr", "misr", "mcc", "frobenius"]
+
+
+def run_table4(args, datasets: int = 50):
+    """The estimation study's AR(1) and AR(4) rows of Table 4: 50 seeded
+    datasets per network (p = 500, n = 250, X ~ N(0, Theta^-1)), each level
+    (SPMESL-2: lambda_univ, SPMESL-4: lambda_ub, SPMESL-P: lambda_pb) one FP64
+    batch of the 50 fits, measures on the GPU (spmesl_support_metrics), means
+    and standard errors against the printed ones."""
+    import numpy as np
+    import torch
+
+    import paper_2203_15031_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sp.lib()
+    p, n = 500, 250
+    with open(os.path.join(ROOT, TABLE4_FIXTURE)) as fh:
+        table4 = json.load(fh)
+    rules = {"SPMESL-2": sp.LAMBDA_UNIV, "SPMESL-4": sp.LAMBDA_UB, "SPMESL-P": sp.LAMBDA_PB}
+    rows, solve_ms = [], []
+    for kind in ("ar1_paper", "ar4"):
+        theta = synth.make_theta(kind, p, np.random.default_rng(0))
+        theta_d = torch.from_numpy(theta).to(dev)
+        Xs = [torch.from_numpy(synth.sample_x(theta, n, np.random.default_rng(7000 + s),
+                                              dtype=np.float64)).to(dev)
+              for s in range(datasets)]
+        for name, rule in rules.items():
+            lam = sp.spmesl_lambda(rule, n, p)
+            bt = sp.Batch([(X, lam) for X in Xs], kind="X", precision="fp64", tol=1e-8,
+                          maxit=1000)
+            bt.run()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bt.run()
+            statuses, _ = bt.result()
+            solve_ms.append((time.perf_counter() - t0) * 1e3)
+            vals = []
+            for T in bt.Theta:
+                m = sp.support_metrics(T, theta_d)
+                vals.append([m["n_edges_hat"], 100 * m["sen"], 100 * m["spe"], 100 * m["fdr"],
+                             100 * m["misr"], 100 * m["mcc"], m["frobenius"]])
+            v = np.array(vals)
+            mean, se = v.mean(0), v.std(0, ddof=1) / math.sqrt(datasets)
+            row = next(r for r in table4["rows"] if r["network"] == kind and r["method"] == name)
+            paper, paper_se = row["mean"], row["se"]
+            rows.append({"network": kind, "method": name, "lambda0": lam,
+                         "statuses_ok": int(sum(s == sp.SPMESL_OK for s in statuses)),
+                         "ours": dict(zip(TABLE4_KEYS, [round(float(x), 4) for x in mean])),
+                         "ours_se": dict(zip(TABLE4_KEYS, [round(float(x), 4) for x in se])),
+                         "paper": dict(zip(TABLE4_KEYS, paper)),
+                         "paper_se": dict(zip(TABLE4_KEYS, paper_se))})
+            bt.close()
+    line = {"metric": "estimation measures vs Table 4 (AR(1), AR(4); p=500, n=250, 50 datasets)",
+            "workload": "table4", "precision": "fp64", "tol": 1e-8,
+            "batch_ms_50_fits": [round(x, 2) for x in solve_ms], "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_regression(args):
     """One scaled-lasso regression per step (spmesl_scaled_lasso): Erdos-Renyi
     predictors p=2000, n=200, y = X beta + noise with 10 active coefficients;
@@ -787,6 +937,10 @@ def main():
         run_serve(args)
     elif args.workload == "regression":
         run_regression(args)
+    elif args.workload == "batch256":
+        run_batch256(args)
+    elif args.workload == "table4":
+        run_table4(args)
     elif args.workload != WORKLOAD:
         run_single(args)
     else:

@@ -272,6 +272,35 @@ spmesl_status spmesl_scaled_lasso(const void* X, const void* y, int n, int p, do
                                   size_t ws_bytes, void* stream);
 
 /*
+ * Support-recovery and estimation-error measures of an estimate against the
+ * true precision matrix, as defined in Section 4.2 (the estimation study):
+ * over the pairs j < k an entry is an edge when it is not exactly zero;
+ *   SEN = TP/(TP+FN), SPE = TN/(TN+FP), FDR = FP/(TP+FP),
+ *   MISR = (FP+FN)/(p(p-1)/2),
+ *   MCC = (TP TN - FP FN)/sqrt((TP+FP)(TP+FN)(TN+FP)(TN+FN)),
+ * and the Frobenius norm of Theta_hat - Theta_true over all entries.  A ratio
+ * with a zero denominator is NaN.  The paper has no GPU counterpart: this is
+ * the evaluation of its estimates.
+ *   Theta_hat, Theta_true  p x p FP64, row-major, device.
+ *   out        host pointer; the call synchronises `stream`.
+ *   workspace  spmesl_metrics_workspace_bytes() bytes, 256-byte aligned.
+ * The sums are formed in a fixed order (deterministic).
+ * Errors: EINVAL (NULL pointers, p < 2, short or misaligned workspace), ECUDA.
+ */
+typedef struct {
+    int64_t tp, fp, tn, fn;
+    int64_t n_edges_hat;        /* TP + FP */
+    int64_t n_edges_true;       /* TP + FN */
+    double frobenius;           /* ||Theta_hat - Theta_true||_F */
+    double sen, spe, fdr, misr, mcc;
+} spmesl_metrics;
+
+size_t spmesl_metrics_workspace_bytes(void);
+spmesl_status spmesl_support_metrics(const double* Theta_hat, const double* Theta_true, int p,
+                                     spmesl_metrics* out, void* workspace, size_t ws_bytes,
+                                     void* stream);
+
+/*
  * End-to-end solve from HOST data: copies X_host to the device, builds S
  * (spmesl_gram), fits (spmesl_fit), copies Theta and sigma back to the host
  * buffers and synchronises `stream`.

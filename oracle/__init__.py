@@ -153,6 +153,38 @@ def columns(S: np.ndarray, cols, lambda0: float, tol: float = 1e-8, maxit: int =
 
 
 # ---------------------------------------------------------------------------
+# Estimation measures of the estimation study (Section 4.2).
+# ---------------------------------------------------------------------------
+
+def support_metrics(theta_hat: np.ndarray, theta_true: np.ndarray) -> dict:
+    """TP, FP, TN, FN over the pairs j < k (an entry is an edge when it is not
+    exactly zero); SEN, SPE, FDR, MISR, MCC from them; the Frobenius norm of
+    theta_hat - theta_true over all entries.  Ratios with a zero denominator
+    are NaN."""
+    A = np.asarray(theta_hat, dtype=np.float64)
+    B = np.asarray(theta_true, dtype=np.float64)
+    p = A.shape[0]
+    tp = fp = tn = fn = 0
+    for j in range(p):
+        for k in range(j + 1, p):
+            e, t = A[j, k] != 0.0, B[j, k] != 0.0
+            tp += e and t
+            fp += e and not t
+            tn += (not e) and (not t)
+            fn += (not e) and t
+
+    def ratio(a, b):
+        return a / b if b > 0 else float("nan")
+
+    return dict(tp=tp, fp=fp, tn=tn, fn=fn, n_edges_hat=tp + fp, n_edges_true=tp + fn,
+                frobenius=float(math.sqrt(float(np.sum((A - B) ** 2)))),
+                sen=ratio(tp, tp + fn), spe=ratio(tn, tn + fp), fdr=ratio(fp, tp + fp),
+                misr=(fp + fn) / (p * (p - 1) / 2.0),
+                mcc=ratio(tp * tn - fp * fn,
+                          math.sqrt(float(tp + fp) * (tp + fn) * (tn + fp) * (tn + fn))))
+
+
+# ---------------------------------------------------------------------------
 # Penalty levels (Section 2.1 and Section 2.3, Eqs. (10)-(11)).
 # ---------------------------------------------------------------------------
 

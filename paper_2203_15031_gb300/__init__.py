@@ -26,6 +26,7 @@ __all__ = [
     "spmesl_max_p", "spmesl_gram_workspace_bytes", "spmesl_gram", "spmesl_fit_workspace_bytes",
     "spmesl_fit", "spmesl_fit_noalloc", "spmesl_fit_result", "spmesl_fit_coefficients",
     "spmesl_scaled_lasso_workspace_bytes", "spmesl_scaled_lasso",
+    "spmesl_metrics_workspace_bytes", "spmesl_support_metrics",
     "spmesl_solve_workspace_bytes",
     "spmesl_solve", "spmesl_batch_create", "spmesl_batch_workspace_bytes", "spmesl_batch_run",
     "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_destroy", "Problem", "Batch",
@@ -75,6 +76,18 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
 
 
+class Metrics(ctypes.Structure):
+    """spmesl_metrics (include/spmesl.h)."""
+    _fields_ = [("tp", ctypes.c_int64), ("fp", ctypes.c_int64), ("tn", ctypes.c_int64),
+                ("fn", ctypes.c_int64), ("n_edges_hat", ctypes.c_int64),
+                ("n_edges_true", ctypes.c_int64), ("frobenius", ctypes.c_double),
+                ("sen", ctypes.c_double), ("spe", ctypes.c_double), ("fdr", ctypes.c_double),
+                ("misr", ctypes.c_double), ("mcc", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SpmeslError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -100,6 +113,8 @@ _SIGS = {
     "spmesl_fit_result": (_i32, [_vp, _i32, _i32, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_coefficients": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "spmesl_scaled_lasso_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "spmesl_metrics_workspace_bytes": (_sz, []),
+    "spmesl_support_metrics": (_i32, [_vp, _vp, _i32, ctypes.POINTER(Metrics), _vp, _sz, _vp]),
     "spmesl_scaled_lasso": (_i32, [_vp, _vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts),
                                    _vp, _vp, ctypes.POINTER(Stats), _vp, _sz, _vp]),
     "spmesl_batch_create": (_i32, [ctypes.POINTER(Problem), _i32, _dbl, _i32,
@@ -259,6 +274,15 @@ def spmesl_scaled_lasso(X, y, n, p, lambda0, tol, maxit, opts, beta, sigma, stat
                                      _ptr(workspace), ws_bytes, _stream(stream))
 
 
+def spmesl_metrics_workspace_bytes() -> int:
+    return lib().spmesl_metrics_workspace_bytes()
+
+
+def spmesl_support_metrics(Theta_hat, Theta_true, p, out, workspace, ws_bytes, stream=None) -> int:
+    return lib().spmesl_support_metrics(_ptr(Theta_hat), _ptr(Theta_true), p, ctypes.byref(out),
+                                        _ptr(workspace), ws_bytes, _stream(stream))
+
+
 def spmesl_solve_workspace_bytes(n: int, p: int, precision: int) -> int:
     return lib().spmesl_solve_workspace_bytes(n, p, precision)
 
@@ -317,6 +341,20 @@ def scaled_lasso(X, y, lambda0, tol=1e-6, maxit=1000, precision="fp32", standard
     d = st.as_dict()
     d["status"] = rc
     return beta, float(sigma.item()), d
+
+
+def support_metrics(Theta_hat, Theta_true, stream=None) -> dict:
+    """SEN, SPE, FDR, MISR, MCC, edge counts and Frobenius error of a CUDA FP64
+    estimate against the true precision matrix (Section 4.2)."""
+    _require_cuda()
+    p = Theta_hat.shape[0]
+    nb = spmesl_metrics_workspace_bytes()
+    keep, ws = _workspace(nb, Theta_hat.device)
+    m = Metrics()
+    _check(spmesl_support_metrics(Theta_hat.contiguous(), Theta_true.contiguous(), p, m, ws, nb,
+                                  stream), "spmesl_support_metrics")
+    del keep
+    return m.as_dict()
 
 
 def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=True,

@@ -89,6 +89,118 @@ def theta_hub(p: int, rng: np.random.Generator, n_hubs: int = 20, links: int = 5
     return _make_pd_unit_diag(T)
 
 
+# ---------------------------------------------------------------------------
+# The four networks of the paper's estimation study (Section 4.2): AR(1),
+# AR(4), scale-free and hub, the last two built from p/100 subnetworks of
+# 100 nodes with the normalisation steps (i)-(iv) after Peng et al. and the
+# magnitude floor 0.1 on nonzero off-diagonal entries.
+# ---------------------------------------------------------------------------
+
+def theta_ar1_paper(p: int) -> np.ndarray:
+    """AR(1) of the estimation study: 1 on the diagonal, 0.48 next to it."""
+    return theta_ar1(p, 0.48)
+
+
+def theta_ar4(p: int) -> np.ndarray:
+    """AR(4): omega_ij = 0.6^|i-j| for |i-j| <= 4, else 0."""
+    T = np.zeros((p, p))
+    for d in range(5):
+        idx = np.arange(p - d)
+        T[idx, idx + d] = 0.6 ** d
+        T[idx + d, idx] = 0.6 ** d
+    return T
+
+
+def _peng_omega(p: int, edges, rng: np.random.Generator) -> np.ndarray:
+    """Steps (i)-(iv): U([-1,-0.5] u [0.5,1]) on the edges and 1 on the
+    diagonal; each row divided by 1.5 times its off-diagonal absolute sum;
+    symmetrised by averaging; unit diagonal."""
+    T = np.eye(p)
+    for i, j in edges:
+        u = rng.uniform(0.5, 1.0) * rng.choice([-1.0, 1.0])
+        T[i, j] = u
+        T[j, i] = u
+    off = np.abs(T).sum(axis=1) - 1.0
+    off[off == 0.0] = 1.0                  # isolated node: its row has no off-diagonal entry
+    T = T / (1.5 * off)[:, None]
+    T = (T + T.T) / 2.0
+    np.fill_diagonal(T, 1.0)
+    return T
+
+
+def _floor_magnitudes(T: np.ndarray, floor: float = 0.1) -> np.ndarray:
+    """Nonzero off-diagonal entries of magnitude below `floor` set to
+    sign * floor."""
+    T = T.copy()
+    off = ~np.eye(T.shape[0], dtype=bool)
+    small = off & (T != 0.0) & (np.abs(T) < floor)
+    T[small] = np.sign(T[small]) * floor
+    return T
+
+
+def ba_tree_edges(m: int, rng: np.random.Generator):
+    """Barabasi-Albert preferential attachment with one edge per new node: node
+    t attaches to an earlier node chosen with probability proportional to its
+    degree (a tree with m - 1 edges)."""
+    edges = [(0, 1)]
+    deg = np.zeros(m)
+    deg[0] = deg[1] = 1.0
+    for t in range(2, m):
+        w = deg[:t] / deg[:t].sum()
+        s = int(rng.choice(t, p=w))
+        edges.append((s, t))
+        deg[s] += 1.0
+        deg[t] += 1.0
+    return edges
+
+
+def hub_edges(m: int, rng: np.random.Generator, n_hubs: int = 10, p_second: float = 0.22):
+    """Hub subnetwork of m nodes: n_hubs hubs; the non-hubs, in random order,
+    join the hubs in turn (every hub gets the same share), and each joins a
+    second, random hub with probability p_second.  Non-hub degrees are 1-2 and
+    hub degrees about (m - n_hubs)(1 + p_second) / n_hubs (11 for m = 100)."""
+    hubs = rng.choice(m, size=n_hubs, replace=False)
+    others = rng.permutation(np.setdiff1d(np.arange(m), hubs))
+    edges = set()
+    for i, v in enumerate(others):
+        first = hubs[i % n_hubs]
+        picks = [first]
+        if rng.random() < p_second:
+            picks.append(rng.choice(hubs[hubs != first]))
+        for h in picks:
+            a, b = (int(h), int(v)) if h < v else (int(v), int(h))
+            edges.add((a, b))
+    return sorted(edges)
+
+
+def _block_network(p: int, rng: np.random.Generator, edge_fn) -> np.ndarray:
+    """p/100 subnetworks of 100 nodes (the last one takes the remainder),
+    each through steps (i)-(iv) and the magnitude floor.  Those steps do not
+    make a hub-like block positive definite (a node's symmetrised row adds
+    up the normalised entries of its neighbours' rows), so a block whose
+    smallest eigenvalue is below 0.1 gets the shift used for the other
+    networks: to smallest eigenvalue 0.1, then unit diagonal."""
+    T = np.zeros((p, p))
+    for s in range(0, p, 100):
+        m = min(100, p - s)
+        if m < 2:
+            T[s, s] = 1.0
+            continue
+        B = _floor_magnitudes(_peng_omega(m, edge_fn(m, rng), rng))
+        if _min_eig(B) < 0.1:
+            B = _make_pd_unit_diag(B)
+        T[s:s + m, s:s + m] = B
+    return T
+
+
+def theta_scale_free(p: int, rng: np.random.Generator) -> np.ndarray:
+    return _block_network(p, rng, ba_tree_edges)
+
+
+def theta_hub_peng(p: int, rng: np.random.Generator) -> np.ndarray:
+    return _block_network(p, rng, hub_edges)
+
+
 def sample_x(theta: np.ndarray, n: int, rng: np.random.Generator,
              dtype=np.float32) -> np.ndarray:
     """X (n x p, row-major) with rows iid N(0, theta^{-1})."""
@@ -109,6 +221,14 @@ def make_theta(kind: str, p: int, rng: np.random.Generator) -> np.ndarray:
         return theta_hub(p, rng)
     if kind == "hub_scaled":
         return theta_hub(p, rng, n_hubs=min(20, max(1, p // 10)), links=min(50, max(1, p // 4)))
+    if kind == "ar1_paper":
+        return theta_ar1_paper(p)
+    if kind == "ar4":
+        return theta_ar4(p)
+    if kind == "scale_free":
+        return theta_scale_free(p, rng)
+    if kind == "hub_peng":
+        return theta_hub_peng(p, rng)
     raise ValueError(f"unknown network kind {kind!r}")
 
 
