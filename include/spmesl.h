@@ -232,6 +232,45 @@ spmesl_status spmesl_fit_noalloc(const void* S, int n, int p, double lambda0, do
 spmesl_status spmesl_fit_result(const void* workspace, int p, int precision,
                                 spmesl_stats* stats, void* stream);
 
+/*
+ * One SPMESL fit from the data in the residual form, without the Gram matrix
+ * (Algorithm 3's residual matrix E = X - X B and the rank-1 update of
+ * Proposition 2, run per column with the cyclic order and the per-column
+ * stopping rule of Algorithm 1).  Column j keeps its residual
+ * e_j = x_j - X b_j; the gradient of coordinate k is x_k' e_j / n and a move
+ * updates e_j -= x_k delta.  sigma_j^2 = ||e_j||^2 / n (Eq. (14)) in FP64 from
+ * a residual recomputed from the data.  The estimate is the one spmesl_gram +
+ * spmesl_fit computes; the iterates are plain cyclic sweeps (the covariance
+ * form also sweeps the current support alone before each full sweep).
+ * Memory: the scaled data twice (n x p and p x n) and the p x p coefficients,
+ * against S, the standardised S and two p x p matrices in the covariance form.
+ *   X          n x p data, row-major with leading dimension ldx >= p, device,
+ *              FP64 for SPMESL_FP64, FP32 otherwise (SPMESL_MIXED runs as
+ *              SPMESL_FP32: there is no Gram to build).  Read only.
+ *   n          sample size, 1 <= n <= 16384.
+ *   lambda0, tol, maxit, Theta, sigma, stats: as spmesl_fit.
+ *   opts       precision, standardize (columns scaled to unit variance and
+ *              the result mapped back, Proposition 1), center (subtract
+ *              column means, Section 2.2), lambda_rule, warps_per_block,
+ *              record_phase_times; inner_rule must be SPMESL_INNER_COLUMN.
+ *   workspace  spmesl_fit_residual_workspace_bytes(n, p, precision) bytes,
+ *              256-byte aligned, owned by the caller; must not be reused
+ *              until the fit has completed on `stream`.  spmesl_fit_result
+ *              reads its status; spmesl_fit_coefficients does not apply.
+ * A column whose support outgrows 256 coefficients stops and reports
+ * NOT_CONVERGED with its last iterate.
+ * Errors: EINVAL (NULL pointers, p < 2, n outside [1, 16384], ldx < p,
+ * lambda0 <= 0, tol <= 0, maxit < 1, inner_rule JOINT, short or misaligned
+ * workspace, sizes whose per-warp shared memory exceeds the block limit);
+ * ECUDA.  Device-detected: ENONFINITE (non-finite X or a column of zero
+ * variance; Theta untouched), EDEGENERATE, NOT_CONVERGED.
+ */
+size_t spmesl_fit_residual_workspace_bytes(int n, int p, int precision);
+spmesl_status spmesl_fit_residual(const void* X, int n, int p, int ldx, double lambda0,
+                                  double tol, int maxit, const spmesl_opts* opts, double* Theta,
+                                  double* sigma, spmesl_stats* stats, void* workspace,
+                                  size_t ws_bytes, void* stream);
+
 /* Copy the coefficients of the last fit in `workspace` to B (p x p FP64
  * device buffer, original scale, B[j*p + k] = b_jk, zero diagonal). */
 spmesl_status spmesl_fit_coefficients(const void* workspace, int p, int precision, double* B,

@@ -25,6 +25,7 @@ __all__ = [
     "spmesl_default_opts", "spmesl_status_string", "spmesl_version", "spmesl_lambda",
     "spmesl_max_p", "spmesl_gram_workspace_bytes", "spmesl_gram", "spmesl_fit_workspace_bytes",
     "spmesl_fit", "spmesl_fit_noalloc", "spmesl_fit_result", "spmesl_fit_coefficients",
+    "spmesl_fit_residual_workspace_bytes", "spmesl_fit_residual",
     "spmesl_scaled_lasso_workspace_bytes", "spmesl_scaled_lasso",
     "spmesl_metrics_workspace_bytes", "spmesl_support_metrics",
     "spmesl_solve_workspace_bytes",
@@ -32,7 +33,7 @@ __all__ = [
     "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_destroy", "Problem", "Batch",
     "spmesl_ctx_create", "spmesl_submit", "spmesl_poll", "spmesl_ctx_query", "spmesl_ctx_destroy",
     "Server",
-    "gram", "fit", "solve",
+    "gram", "fit", "fit_residual", "solve",
 ]
 
 SPMESL_OK, SPMESL_NOT_CONVERGED = 0, 1
@@ -111,6 +112,10 @@ _SIGS = {
     "spmesl_fit_noalloc": (_i32, [_vp, _i32, _i32, _dbl, _dbl, _i32, ctypes.POINTER(Opts), _vp,
                                   _vp, ctypes.POINTER(Stats), _vp]),
     "spmesl_fit_result": (_i32, [_vp, _i32, _i32, ctypes.POINTER(Stats), _vp]),
+    "spmesl_fit_residual_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "spmesl_fit_residual": (_i32, [_vp, _i32, _i32, _i32, _dbl, _dbl, _i32,
+                                   ctypes.POINTER(Opts), _vp, _vp, ctypes.POINTER(Stats), _vp,
+                                   _sz, _vp]),
     "spmesl_fit_coefficients": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "spmesl_scaled_lasso_workspace_bytes": (_sz, [_i32, _i32, _i32]),
     "spmesl_metrics_workspace_bytes": (_sz, []),
@@ -252,6 +257,19 @@ def spmesl_fit_noalloc(S, n, p, lambda0, tol, maxit, opts, Theta, sigma, stats,
                                     _stream(stream))
 
 
+def spmesl_fit_residual_workspace_bytes(n: int, p: int, precision: int) -> int:
+    return lib().spmesl_fit_residual_workspace_bytes(n, p, precision)
+
+
+def spmesl_fit_residual(X, n, p, ldx, lambda0, tol, maxit, opts, Theta, sigma, stats, workspace,
+                        ws_bytes, stream=None) -> int:
+    return lib().spmesl_fit_residual(_ptr(X), n, p, ldx, lambda0, tol, maxit,
+                                     ctypes.byref(opts) if opts is not None else None,
+                                     _ptr(Theta), _ptr(sigma),
+                                     ctypes.byref(stats) if stats is not None else None,
+                                     _ptr(workspace), ws_bytes, _stream(stream))
+
+
 def spmesl_fit_result(workspace, p, precision, stats, stream=None) -> int:
     return lib().spmesl_fit_result(_ptr(workspace), p, precision,
                                    ctypes.byref(stats) if stats is not None else None,
@@ -355,6 +373,37 @@ def support_metrics(Theta_hat, Theta_true, stream=None) -> dict:
                                   stream), "spmesl_support_metrics")
     del keep
     return m.as_dict()
+
+
+def fit_residual(X, lambda0, tol=1e-6, maxit=1000, precision="fp32", standardize=True,
+                 center=False, lambda_rule=LAMBDA_GIVEN, warps_per_block=0,
+                 record_phase_times=False, stream=None):
+    """One fit from a CUDA data tensor X (n x p) in the residual form (no Gram
+    matrix).  Synchronises and returns (Theta, sigma, stats_dict)."""
+    import torch
+    _require_cuda()
+    prec = _prec(precision)
+    n, p = X.shape
+    X = X.contiguous()
+    opts = spmesl_default_opts()
+    opts.precision = prec
+    opts.standardize = int(bool(standardize))
+    opts.center = int(bool(center))
+    opts.lambda_rule = int(lambda_rule)
+    opts.warps_per_block = int(warps_per_block)
+    opts.record_phase_times = int(bool(record_phase_times))
+    Theta = torch.empty((p, p), dtype=torch.float64, device=X.device)
+    sigma = torch.empty(p, dtype=torch.float64, device=X.device)
+    nb = spmesl_fit_residual_workspace_bytes(n, p, prec)
+    if nb == 0:
+        raise SpmeslError(SPMESL_EINVAL, "spmesl_fit_residual_workspace_bytes")
+    keep, ws = _workspace(nb, X.device)
+    st = Stats()
+    rc = spmesl_fit_residual(X, n, p, p, lambda0, tol, maxit, opts, Theta, sigma, st, ws, nb,
+                             stream)
+    del keep
+    _check(rc, "spmesl_fit_residual", ok=(SPMESL_OK, SPMESL_NOT_CONVERGED))
+    return Theta, sigma, st.as_dict()
 
 
 def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=True,

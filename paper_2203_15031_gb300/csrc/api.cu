@@ -258,6 +258,68 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
     return rs;
 }
 
+size_t spmesl_fit_residual_workspace_bytes(int n, int p, int precision) {
+    if (!valid_precision(precision) || !residual_sizes_ok(n, p, precision)) return 0;
+    return res_layout(n, p, precision).total;
+}
+
+spmesl_status spmesl_fit_residual(const void* X, int n, int p, int ldx, double lambda0,
+                                  double tol, int maxit, const spmesl_opts* opts, double* Theta,
+                                  double* sigma, spmesl_stats* stats, void* workspace,
+                                  size_t ws_bytes, void* stream) {
+    const spmesl_opts o = resolve_opts(opts);
+    if (!X || !Theta || !sigma || !workspace || p < 2 || n < 1 || ldx < p || maxit < 1 ||
+        !(tol > 0.0) || !valid_precision(o.precision))
+        return SPMESL_EINVAL;
+    if (o.inner_rule != SPMESL_INNER_COLUMN) return SPMESL_EINVAL;
+    if (!residual_sizes_ok(n, p, o.precision)) return SPMESL_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return SPMESL_EINVAL;
+    if (ws_bytes < res_layout(n, p, o.precision).total) return SPMESL_EINVAL;
+    double lam = lambda0;
+    if (o.lambda_rule != SPMESL_LAMBDA_GIVEN) lam = spmesl_lambda(o.lambda_rule, n, p);
+    if (!(lam > 0.0) || !isfinite(lam)) return SPMESL_EINVAL;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+    }
+    ResLaunch f;
+    f.X = X;
+    f.n = n;
+    f.p = p;
+    f.ldx = ldx;
+    f.lambda0 = lam;
+    f.tol = tol;
+    f.maxit = maxit;
+    f.precision = o.precision;
+    f.standardize = o.standardize ? 1 : 0;
+    f.center = o.center ? 1 : 0;
+    f.warps_per_block = o.warps_per_block;
+    f.Theta = Theta;
+    f.sigma_out = sigma;
+    f.ws = static_cast<unsigned char*>(workspace);
+    f.phase_events = o.record_phase_times ? phase_events_for(workspace) : nullptr;
+    cudaError_t e = launch_fit_residual(f, st);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return from_cuda(e);
+    }
+    if (!stats) return SPMESL_OK;
+    cudaEventRecord(e1, st);
+    spmesl_status rs = spmesl_fit_result(workspace, p, o.precision, stats, stream);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    stats->ms_fit = ms;
+    stats->lambda0 = lam;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rs;
+}
+
 size_t spmesl_scaled_lasso_workspace_bytes(int n, int p, int precision) {
     if (n < 1 || p < 1 || !valid_precision(precision)) return 0;
     return lasso_layout(n, p, precision).total;

@@ -174,14 +174,16 @@ struct ColScan {
 // |S_km| <= 1 (standardised), so |g_k| <= maxabs + sum|delta| since the chunk
 // was scanned.  The margins cover FP32 rounding of the standardised S
 // (|S_km| <= 1 + 2^-22), of every g update (half an ulp of a value below
-// lambda) and of the running sum; after 4096 moves the chunk is always
-// rescanned.  A skipped coordinate therefore has |g_k| < lambda and b_k = 0,
-// so it would not have moved: the sweep is the same as a full scan.
+// lambda) and of the running sum (each of the dm additions since the scan is
+// off by at most 2^-24 of the sum, which only grows); after 4096 moves the
+// chunk is always rescanned.  A skipped coordinate therefore has
+// |g_k| < lambda and b_k = 0, so it would not have moved: the sweep is the
+// same as a full scan.
 __device__ __forceinline__ bool chunk_skippable(const ChunkInfo& c, const ColScan& cs, float lam) {
     const unsigned dm = cs.nmoves - c.moves_at;
     if (c.nsupp != 0 || dm > 4096u) return false;
     const float bound = c.maxabs + (cs.dsum - c.dsum_at) * (1.0f + 0x1p-10f) +
-                        cs.dsum * 0x1p-21f + (float)dm * lam * 0x1p-20f;
+                        cs.dsum * (float)(dm + 2u) * 0x1p-23f + (float)dm * lam * 0x1p-20f;
     return bound < lam;
 }
 

@@ -84,6 +84,35 @@ inline FitLayout fit_layout(int p, int precision) {
     return L;
 }
 
+// Byte offsets of the residual-form workspace (spmesl_fit_residual): the
+// control block first (spmesl_fit_result reads it there), then the per-column
+// vectors, the scaled data W (ldn x ldp) and its transpose Wt (p x ldn), and
+// the coefficients BT (p x ldp).
+struct ResLayout {
+    int ldn, ldp;
+    size_t ctrl, cs, sigma, col_status, mu, wscale, diag, W, Wt, BT, total;
+};
+
+inline ResLayout res_layout(int n, int p, int precision) {
+    ResLayout L{};
+    const size_t s = (size_t)elem_size(precision);
+    L.ldn = padded_ld(n);
+    L.ldp = padded_ld(p);
+    size_t off = 0;
+    L.ctrl = off;        off += 256;
+    L.cs = off;          off += align_up((size_t)p * 8, 256);
+    L.sigma = off;       off += align_up((size_t)p * 8, 256);
+    L.col_status = off;  off += align_up((size_t)p * 4, 256);
+    L.mu = off;          off += align_up((size_t)p * 8, 256);
+    L.wscale = off;      off += align_up((size_t)p * 8, 256);
+    L.diag = off;        off += align_up((size_t)p * s, 256);
+    L.W = off;           off += align_up((size_t)L.ldn * L.ldp * s, 256);
+    L.Wt = off;          off += align_up((size_t)p * L.ldn * s, 256);
+    L.BT = off;          off += align_up((size_t)p * L.ldp * s, 256);
+    L.total = off;
+    return L;
+}
+
 // 16-byte vector of T.
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
@@ -124,6 +153,20 @@ struct FitLaunch {
     double* beta_out = nullptr;
 };
 cudaError_t launch_fit(const FitLaunch& f, cudaStream_t st);
+// One fit in the residual form (residual.cu): X n x p (ld ldx) on the device.
+struct ResLaunch {
+    const void* X;
+    int n, p, ldx;
+    double lambda0, tol;
+    int maxit;
+    int precision, standardize, center, warps_per_block;
+    double* Theta;
+    double* sigma_out;
+    unsigned char* ws;
+    cudaEvent_t* phase_events;   // nullptr, or 3 events: before CD, after CD, after Theta
+};
+cudaError_t launch_fit_residual(const ResLaunch& f, cudaStream_t st);
+bool residual_sizes_ok(int n, int p, int precision);
 cudaError_t launch_export_B(const unsigned char* ws, int p, int precision, double* B,
                             cudaStream_t st);
 int max_p_for(int precision);
