@@ -371,6 +371,24 @@ def run_ours(args):
            "h2d_bytes_per_step": N_DATASETS * n * p * 4,
            "d2h_bytes_per_step": N_DATASETS * (p * p * 8 + p * 8),
            "pipeline": "two batches on two streams in turn; host waits at the end"}
+    # The bound of the end-to-end number: the device-to-host link, measured as
+    # one more copy of a step's Theta bytes into pinned host memory (best of 3)
+    lk_src = torch.zeros(N_DATASETS * p * p, dtype=torch.float64, device=dev)
+    lk_dst = torch.empty(N_DATASETS * p * p, dtype=torch.float64).pin_memory()
+    lk = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lk_dst.copy_(lk_src, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        lk.append(a.elapsed_time(b))
+    link_gbs = lk_src.numel() * 8 / (min(lk) / 1e3) / 1e9
+    ceiling = world * N_DATASETS * link_gbs * 1e9 / e2e["d2h_bytes_per_step"]
+    e2e["link_d2h_gbs"] = link_gbs
+    e2e["link_ceiling_solves_per_s"] = ceiling
+    e2e["frac_of_link_ceiling"] = e2e["value"] / ceiling
+    del lk_src, lk_dst
 
     if rank == 0:
         hbm, which = _peaks()
