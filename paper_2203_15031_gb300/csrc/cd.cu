@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(512) cd_column_lazy_kernel(CDArgs<T> a) {
         }
         j = __shfl_sync(FULL_MASK, j, 0);
         if (j >= a.p) break;
-        if (!solve_column_lazy<T, STD>(j, wsm, a, cnt) && lane == 0)
+        if (!solve_column_lazy<T, STD, true>(j, wsm, a, cnt) && lane == 0)
             a.ovf_list[atomicAdd(a.ovf_count, 1)] = j;
         __syncwarp();
     }
