@@ -178,10 +178,15 @@ struct ColScan {
 // off by at most 2^-24 of the sum, which only grows); after 4096 moves the
 // chunk is always rescanned.  A skipped coordinate therefore has
 // |g_k| < lambda and b_k = 0, so it would not have moved: the sweep is the
-// same as a full scan.
-__device__ __forceinline__ bool chunk_skippable(const ChunkInfo& c, const ColScan& cs, float lam) {
+// same as a full scan.  With `frozen` (a sweep that leaves the support's
+// values as they are, see solve_column_lazy) a chunk holding support may be
+// skipped too: maxabs covers the chunk's coordinates that were zero when it
+// was scanned, and a coordinate that has left the support since then marks
+// its chunk for a rescan (maxabs = infinity).
+__device__ __forceinline__ bool chunk_skippable(const ChunkInfo& c, const ColScan& cs, float lam,
+                                                bool frozen = false) {
     const unsigned dm = cs.nmoves - c.moves_at;
-    if (c.nsupp != 0 || dm > 4096u) return false;
+    if ((c.nsupp != 0 && !frozen) || dm > 4096u) return false;
     const float bound = c.maxabs + (cs.dsum - c.dsum_at) * (1.0f + 0x1p-10f) +
                         cs.dsum * (float)(dm + 2u) * 0x1p-23f + (float)dm * lam * 0x1p-20f;
     return bound < lam;
@@ -276,10 +281,10 @@ __device__ T sweep_column(int j, T* __restrict__ g, T* __restrict__ b, const CDA
     return maxd;
 }
 
-// Mark every chunk "must scan" (a chunk with nsupp != 0 is never skipped).
+// Mark every chunk "must scan" (maxabs = infinity fails every skip test).
 __device__ __forceinline__ void reset_chunks(ColScan& cs, int ldp) {
     const int nc = (ldp + CHUNK - 1) / CHUNK;
-    for (int c = threadIdx.x & 31; c < nc; c += 32) cs.ci[c] = ChunkInfo{0.f, 0.f, 0u, 1};
+    for (int c = threadIdx.x & 31; c < nc; c += 32) cs.ci[c] = ChunkInfo{INFINITY, 0.f, 0u, 1};
     cs.dsum = 0.f;
     cs.nmoves = 0u;
 }
@@ -628,20 +633,24 @@ __device__ __forceinline__ void load4g(const T* __restrict__ src, T (&v)[4]) {
 // summary and the column's running sums, so the lanes test 32 chunks at once.
 // The mask stays valid until a move changes the running sums.
 template <bool STD>
-__device__ __forceinline__ unsigned chunks_to_scan(const ColScan& cs, int from, int nch, float lam) {
+__device__ __forceinline__ unsigned chunks_to_scan(const ColScan& cs, int from, int nch, float lam,
+                                                   bool frozen) {
     const int ci = from + (int)(threadIdx.x & 31);
     bool need = ci < nch;
     if constexpr (STD) {
-        if (need) need = !chunk_skippable(cs.ci[ci], cs, lam);
+        if (need) need = !chunk_skippable(cs.ci[ci], cs, lam, frozen);
     }
     return __ballot_sync(FULL_MASK, need);
 }
 
 // One sweep; returns max |delta b|.  Sets `overflow` and stops early if the
-// support list is full.
+// support list is full.  With `frozen` the coordinates in the support keep
+// their values and only the others are updated (a coordinate that enters is
+// not revisited in the same sweep).
 template <typename T, bool STD>
 __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
-                               unsigned long long& moves, ColScan& cs, bool& overflow) {
+                               unsigned long long& moves, ColScan& cs, bool& overflow,
+                               bool frozen) {
     const int lane = threadIdx.x & 31;
     const int p = a.p;
     const int ldp = a.ldp;
@@ -650,12 +659,12 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
     T maxd = T(0);
     int e0 = 0;                                   // first support entry with idx >= cb
     int mbase = 0;
-    unsigned mask = chunks_to_scan<STD>(cs, 0, nch, (float)lam);
+    unsigned mask = chunks_to_scan<STD>(cs, 0, nch, (float)lam, frozen);
     for (;;) {
         if (mask == 0u) {
             mbase += 32;
             if (mbase >= nch) break;
-            mask = chunks_to_scan<STD>(cs, mbase, nch, (float)lam);
+            mask = chunks_to_scan<STD>(cs, mbase, nch, (float)lam, frozen);
             continue;
         }
         const int ci = mbase + __ffs(mask) - 1;
@@ -699,7 +708,7 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
             for (int t = 0; t < SCAN_V; ++t) {
                 const int k = k0 + t;
                 nbv[t] = bv[t];
-                if (k >= cursor && k < p && k != j) {
+                if (k >= cursor && k < p && k != j && !(frozen && bv[t] != T(0))) {
                     T nb;
                     if constexpr (STD) {
                         nb = soft<T>(acc[t] + bv[t], lam);                 // S_kk = 1
@@ -764,7 +773,7 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
             if (cs.nmoves != nmoves0) {
                 mbase = ci + 1;
                 if (mbase >= nch) break;
-                mask = chunks_to_scan<STD>(cs, mbase, nch, (float)lam);
+                mask = chunks_to_scan<STD>(cs, mbase, nch, (float)lam, frozen);
             }
         } else {
             __syncwarp();
@@ -780,13 +789,17 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
 // gathered once into shared memory (column k at saa + k ACT_MAX).  Every move
 // is added to the column's running sums, so the chunk skip test stays exact
 // for the coordinates outside A.  Coordinates that reach zero leave the
-// support.  Returns the sweeps done (0 when A is empty or larger than ACT_MAX).
+// support and mark their chunk for a rescan.  Returns the sweeps done (0 when
+// A is empty or larger than ACT_MAX); `conv` tells whether the last sweep
+// moved nothing by tol (true for an empty A, false when A is too large).
 template <typename T, bool STD>
 __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* __restrict__ saa,
-                            unsigned long long& moves, ColScan& cs) {
+                            unsigned long long& moves, ColScan& cs, bool& conv) {
     const int lane = threadIdx.x & 31;
     const int n = s.n;
+    conv = n <= ACT_MAX;
     if (n == 0 || n > ACT_MAX) return 0;
+    conv = false;
     const int ldp = a.ldp;
 #pragma unroll 8
     for (int t = lane; t < n * n; t += 32) {
@@ -824,10 +837,14 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
                 ++cs.nmoves;
             }
         }
-        if ((double)md < a.tol) break;
+        if ((double)md < a.tol) {
+            conv = true;
+            break;
+        }
     }
     // write back, dropping coordinates at zero (the list stays sorted)
     const bool keep = lane < n && b != T(0);
+    if (lane < n && b == T(0)) cs.ci[my / CHUNK].maxabs = INFINITY;
     const unsigned km = __ballot_sync(FULL_MASK, keep);
     const int pos = __popc(km & ((1u << lane) - 1u));
     __syncwarp();
@@ -889,10 +906,15 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
         const T lam = (T)(sigma * a.lambda0);
         bool inner_ok = false;
         for (int m = 0; m < a.maxit; ++m) {
-            // converge on the support first, then a full sweep decides (the
-            // stop rule of Algorithm 1: a full sweep with max |delta| < tol)
-            cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.act_moves, cs);
-            const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow);
+            // converge on the support first; then, if that converged, a
+            // sweep over the other coordinates with the support held (its
+            // chunks skippable by the bound) decides: the lasso has converged
+            // when the support's last sweep and this sweep both moved nothing
+            // by tol.  Otherwise a full sweep of every coordinate decides (the
+            // stop rule of Algorithm 1).
+            bool conv;
+            cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.act_moves, cs, conv);
+            const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow, conv);
             ++cnt.sweeps;
             if (overflow) return false;
             if ((double)md < a.tol) {
