@@ -165,14 +165,21 @@ struct ChunkInfo {
 // Scan state of one column solve (warp-uniform).
 struct ColScan {
     ChunkInfo* ci;
-    float dsum;          // sum of |delta| over all moves of this column so far
-    unsigned nmoves;     // number of those moves
+    float dsum;          // running sum of the l1 size of every change of b_j so far: one
+                         // move's |delta|, or an active-set phase's net change
+    unsigned nmoves;     // number of those changes
+    float bl1;           // lazy solver: an upper bound of ||b_j||_1 (0 elsewhere)
 };
 
 // A chunk with no support can be skipped when no coordinate in it can reach
 // the threshold: each move delta_m at row m changes g_k by -S_km delta_m with
 // |S_km| <= 1 (standardised), so |g_k| <= maxabs + sum|delta| since the chunk
-// was scanned.  The margins cover FP32 rounding of the standardised S
+// was scanned (and a change of several coefficients at once moves g_k by at
+// most its l1 size).  The lazy solver forms g_k afresh from S rows at every
+// scan: each of the two computations (then and now) is off by at most
+// 384 * 2^-24 (1 + ||b||_1) (up to 256 support rows and 128 moves in a
+// chunk, |S| <= 1), the last term below with ||b_then||_1 <=
+// ||b_now||_1 + the change since.  The margins cover FP32 rounding of the standardised S
 // (|S_km| <= 1 + 2^-22), of every g update (half an ulp of a value below
 // lambda) and of the running sum (each of the dm additions since the scan is
 // off by at most 2^-24 of the sum, which only grows); after 4096 moves the
@@ -187,9 +194,16 @@ __device__ __forceinline__ bool chunk_skippable(const ChunkInfo& c, const ColSca
                                                 bool frozen = false) {
     const unsigned dm = cs.nmoves - c.moves_at;
     if ((c.nsupp != 0 && !frozen) || dm > 4096u) return false;
-    const float bound = c.maxabs + (cs.dsum - c.dsum_at) * (1.0f + 0x1p-10f) +
-                        cs.dsum * (float)(dm + 2u) * 0x1p-23f + (float)dm * lam * 0x1p-20f;
+    const float dd = cs.dsum - c.dsum_at;
+    const float bound = c.maxabs + dd * (1.0f + 0x1p-10f) + cs.dsum * (float)(dm + 2u) * 0x1p-23f +
+                        (float)dm * lam * 0x1p-20f + (1.0f + cs.bl1 + dd) * 0x1p-14f;
     return bound < lam;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
 }
 
 template <typename T, bool STD>
@@ -287,6 +301,7 @@ __device__ __forceinline__ void reset_chunks(ColScan& cs, int ldp) {
     for (int c = threadIdx.x & 31; c < nc; c += 32) cs.ci[c] = ChunkInfo{INFINITY, 0.f, 0u, 1};
     cs.dsum = 0.f;
     cs.nmoves = 0u;
+    cs.bl1 = 0.f;
 }
 
 // Per-warp scratch for the support list used by the sigma update.
@@ -659,6 +674,11 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
     T maxd = T(0);
     int e0 = 0;                                   // first support entry with idx >= cb
     int mbase = 0;
+    if constexpr (STD) {
+        float l1 = 0.f;
+        for (int e = lane; e < s.n; e += 32) l1 += fabsf((float)s.val[e]);
+        cs.bl1 = warp_sum_f(l1) * (1.0f + 0x1p-16f);
+    }
     unsigned mask = chunks_to_scan<STD>(cs, 0, nch, (float)lam, frozen);
     for (;;) {
         if (mask == 0u) {
@@ -675,7 +695,9 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
         while (e1 < s.n && s.idx[e1] < cb + CHUNK) ++e1;
         const int k0 = cb + lane * SCAN_V;
         const bool in = k0 < ldp;                 // the whole quad is inside the padded row
-        // slice of g: S_jk - sum_{l in support} S_lk b_l
+        // slice of g: S_jk - sum_{l in support} S_lk b_l (four rows in flight;
+        // an L1 prefetch of all the support rows first was measured slower)
+        const T* __restrict__ col = a.SC + k0;    // column k0 of S; row l at col + l ldp
         T acc[SCAN_V] = {T(0), T(0), T(0), T(0)};
         if (in) load4g<T>(Sj + k0, acc);
 #pragma unroll 4
@@ -684,7 +706,7 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
             const T v = s.val[e];
             if (in) {
                 T r[SCAN_V];
-                load4g<T>(a.SC + (size_t)l * ldp + k0, r);
+                load4g<T>(col + (size_t)l * ldp, r);
 #pragma unroll
                 for (int t = 0; t < SCAN_V; ++t) acc[t] = fma(-v, r[t], acc[t]);
             }
@@ -748,6 +770,7 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
             ++moves;
             cs.dsum += fabsf((float)delta);
             ++cs.nmoves;
+            cs.bl1 += fabsf((float)delta);
             // rank-1 update of the rest of this chunk's slice
             if (in) {
                 T r[SCAN_V];
@@ -786,9 +809,9 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
 // coordinate order) over the current support A only, until a sweep moves no
 // coefficient by tol or more (at most maxit sweeps).  Lane m holds coordinate
 // A_m: its b and g_m = S_jm - sum_{l in A} S_ml b_l; the block S_AA is
-// gathered once into shared memory (column k at saa + k ACT_MAX).  Every move
-// is added to the column's running sums, so the chunk skip test stays exact
-// for the coordinates outside A.  Coordinates that reach zero leave the
+// gathered once into shared memory (column k at saa + k ACT_MAX).  The
+// phase's net change of b enters the column's running sums as one change, so
+// the chunk skip test stays exact for the coordinates outside A.  Coordinates that reach zero leave the
 // support and mark their chunk for a rescan.  Returns the sweeps done (0 when
 // A is empty or larger than ACT_MAX); `conv` tells whether the last sweep
 // moved nothing by tol (true for an empty A, false when A is too large).
@@ -808,6 +831,7 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
     }
     const int my = lane < n ? s.idx[lane] : 0;
     T b = lane < n ? s.val[lane] : T(0);
+    const T b_start = b;
     T g = lane < n ? a.SC[(size_t)j * ldp + my] : T(0);
     T skk = T(1);
     if constexpr (!STD) skk = lane < n ? a.diag[my] : T(1);
@@ -833,8 +857,6 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
                 if (lane == k) b = nb;
                 md = fmax(md, fabs(d));
                 ++moves;
-                cs.dsum += fabsf((float)d);
-                ++cs.nmoves;
             }
         }
         if ((double)md < a.tol) {
@@ -842,6 +864,10 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
             break;
         }
     }
+    // the phase enters the running sums as one change: its net l1 size
+    const float net = warp_sum_f(lane < n ? fabsf((float)(b - b_start)) : 0.f);
+    cs.dsum += net * (1.0f + 0x1p-16f);
+    ++cs.nmoves;
     // write back, dropping coordinates at zero (the list stays sorted)
     const bool keep = lane < n && b != T(0);
     if (lane < n && b == T(0)) cs.ci[my / CHUNK].maxabs = INFINITY;
