@@ -169,7 +169,15 @@ spmesl_status spmesl_gram(const void* X, int n, int p, int ldx, int precision, i
  *      applying the rank-1 update g_j -= S_.k delta_kj after every coordinate
  *      that moves (Proposition 2 written on S); sigma_j^2 =
  *      S_jj - 2 b_j'S_.j + b_j'S b_j in FP64 (Eq. (14)); columns whose sigma
- *      changed by less than tol are retired (Section 3.3);
+ *      changed by less than tol are retired (Section 3.3).
+ *      With the per-column rule and the lazy gradient, each column sweeps
+ *      its current support (up to 32 coefficients) to convergence before
+ *      every certifying sweep. That sweep holds the support and updates the
+ *      other coordinates; the lasso at one sigma has converged when both moved
+ *      nothing by tol. The per-column solvers take a safeguarded secant step
+ *      on the fixed point sigma = F(sigma) of Eq. (14) after its first step.
+ *      The stop tests and the returned (b, sigma) pair are those of
+ *      Algorithm 1, so the fit ends at the same fixed point within tol;
  *   3. Omega_1 = -B D (Eq. (4)), min-magnitude symmetrisation (Eq. (9)), and
  *      Omega^o = C Omega^C C.
  *   S          p x p covariance (FP64 for SPMESL_FP64, FP32 otherwise), read only.

@@ -91,3 +91,59 @@ def test_invalid_arguments_rejected_on_host():
     assert sp.spmesl_gram(fake, 0, 5, 5, sp.FP32, 0, fake, 5, fake, 1 << 20, 0) == sp.SPMESL_EINVAL
     assert sp.spmesl_gram(fake, 4, 5, 3, sp.FP32, 0, fake, 5, fake, 1 << 20, 0) == sp.SPMESL_EINVAL
     assert sp.spmesl_gram(fake, 4, 5, 5, 9, 0, fake, 5, fake, 1 << 20, 0) == sp.SPMESL_EINVAL
+
+
+def _al(x):
+    return (x + 255) // 256 * 256
+
+
+def test_residual_workspace_layout_and_limits():
+    """spmesl_fit_residual_workspace_bytes: the control block, six p-vectors,
+    W (ldn x ldp), Wt (p x ldn) and the coefficients (p x ldp), each 256-byte
+    aligned, with ldn = roundup(n, 32) and ldp = roundup(p, 32)."""
+    for prec, s in ((sp.FP32, 4), (sp.FP64, 8), (sp.MIXED, 4)):
+        for n, p in ((200, 2000), (37, 131), (1, 2), (16384, 64)):
+            ldn, ldp = (n + 31) // 32 * 32, (p + 31) // 32 * 32
+            want = (256 + 2 * _al(p * 8) + _al(p * 4) + 2 * _al(p * 8) + _al(p * s)
+                    + _al(ldn * ldp * s) + _al(p * ldn * s) + _al(p * ldp * s))
+            assert sp.spmesl_fit_residual_workspace_bytes(n, p, prec) == want, (prec, n, p)
+    # no p x p covariance: well below the Gram + fit workspaces of the covariance form
+    res = sp.spmesl_fit_residual_workspace_bytes(200, 2000, sp.FP32)
+    cov = sp.spmesl_gram_workspace_bytes(200, 2000, sp.FP32) + sp.spmesl_fit_workspace_bytes(2000, sp.FP32)
+    assert 3 * res < cov + 4 * 2000 * 2000
+    for n, p in ((0, 10), (16385, 10), (10, 1), (-1, 10)):
+        assert sp.spmesl_fit_residual_workspace_bytes(n, p, sp.FP32) == 0
+    assert sp.spmesl_fit_residual_workspace_bytes(10, 10, 7) == 0
+
+
+def test_residual_invalid_arguments_rejected_on_host():
+    o = sp.spmesl_default_opts()
+    fake = 1 << 20        # never dereferenced: validation comes first
+    nb = sp.spmesl_fit_residual_workspace_bytes(30, 50, sp.FP32)
+    ws = 1 << 24          # 256-byte aligned address, never dereferenced
+    ok_args = (fake, 30, 50, 50, 0.2, 1e-6, 100, o, fake, fake, None, ws, nb, 0)
+
+    def call(**kw):
+        a = list(ok_args)
+        names = ["X", "n", "p", "ldx", "lam", "tol", "maxit", "opts", "T", "sig", "st", "ws", "nb",
+                 "stream"]
+        for k, v in kw.items():
+            a[names.index(k)] = v
+        return sp.spmesl_fit_residual(*a)
+
+    assert call(X=None) == sp.SPMESL_EINVAL
+    assert call(n=0) == sp.SPMESL_EINVAL
+    assert call(n=16385) == sp.SPMESL_EINVAL
+    assert call(p=1, ldx=1) == sp.SPMESL_EINVAL
+    assert call(ldx=49) == sp.SPMESL_EINVAL
+    assert call(lam=-0.2) == sp.SPMESL_EINVAL
+    assert call(tol=0.0) == sp.SPMESL_EINVAL
+    assert call(maxit=0) == sp.SPMESL_EINVAL
+    assert call(ws=ws + 16) == sp.SPMESL_EINVAL          # misaligned workspace
+    assert call(nb=nb - 1) == sp.SPMESL_EINVAL           # short workspace
+    joint = sp.spmesl_default_opts()
+    joint.inner_rule = sp.INNER_JOINT
+    assert call(opts=joint) == sp.SPMESL_EINVAL
+    bad_prec = sp.spmesl_default_opts()
+    bad_prec.precision = 9
+    assert call(opts=bad_prec) == sp.SPMESL_EINVAL
