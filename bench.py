@@ -55,6 +55,24 @@ def _env_rank():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the default process group (the slowest
+    rank's time), or x itself when no group of more than one rank is up."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Units per second of the whole job: every rank processed units_per_rank
+    in at most max_ms (weak scaling, no data-path exchange between ranks)."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -275,18 +293,14 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         per = [a.elapsed_time(b) for a, b in ev]
-        total_ms = sum(per)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(per), dev)
         return bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb, act
 
     clk = ClockSampler(local_rank)
     bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb, act = batched(BATCH_PREC, clk)
-    value = world * N_DATASETS * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(N_DATASETS * args.steps, world, total_ms)
     bt32, _, per32, total32, _, _, _, _, _ = batched("fp32")
-    value32 = world * N_DATASETS * args.steps / (total32 / 1e3)
+    value32 = whole_job_rate(N_DATASETS * args.steps, world, total32)
     bt32.close()
 
     # ---- plain path: one fit per launch sequence, serialised on one stream
@@ -362,12 +376,11 @@ def run_ours(args):
         s.synchronize()
     e2e_s = time.perf_counter() - t0
     bt2.close()
+    e2e_s = max_over_ranks(e2e_s, dev)
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
         dist.barrier()
-    e2e = {"value": world * N_DATASETS * args.steps / e2e_s, "unit": "solves/s",
+    e2e = {"value": whole_job_rate(N_DATASETS * args.steps, world, e2e_s * 1e3),
+           "unit": "solves/s",
            "h2d_bytes_per_step": N_DATASETS * n * p * 4,
            "d2h_bytes_per_step": N_DATASETS * (p * p * 8 + p * 8),
            "pipeline": "two batches on two streams in turn; host waits at the end"}
