@@ -1,27 +1,35 @@
 """Benchmark: SPMESL solves/s on one GB300 (and N replicas under torchrun).
 
 Workload (default): Erdos-Renyi network, p = 2000, n = 200, X float32 with
-rows N(0, Theta^{-1}), lambda0 = sqrt(2 log p / n), tol 1e-6, maxit 1000,
-FP32 Gram and FP32 coordinate descent (sigma and Theta in FP64).  One step is
-one pass of the whole path over a batch of ten datasets (seeds 0..9,
-resident in HBM) through the batched C ABI: Gram S = X'X/n, standardisation,
-coordinate descent with sigma updates, Theta assembly and symmetrisation, one
-launch per phase for all ten fits.  The plain path (one spmesl_gram +
-spmesl_fit per fit, serialised on one stream) is timed beside it.
+rows N(0, Theta^{-1}), lambda0 = sqrt(2 log p / n), tol 1e-6, maxit 1000.  One
+step is one pass of the whole path over a batch of ten datasets (seeds 0..9,
+resident in HBM) through the batched C ABI in mixed precision: split-BF16
+Gram S = X'X/n on the tensor cores, standardisation, FP32 coordinate descent
+with FP64 sigma updates, Theta assembly and symmetrisation in FP64, one launch
+per phase for all ten fits.  The same batch with the FP32 Gram and the plain
+path (one FP32 spmesl_gram + spmesl_fit per fit, serialised on one stream) are
+timed beside it.
 
 JSON line fields beyond the base contract:
   e2e          the same metric through the batched C ABI with HOST buffers (the
                ten X copied in from pinned memory, every Theta and sigma copied
-               out, inside the timed region)
+               out, inside the timed region), with the device-to-host link
+               measured in the same run and the ceiling it sets
   plain        solves/s of the one-fit-per-launch path on the same ten datasets
+  batched_fp32 the same batch with the FP32 Gram on the CUDA cores
+  accuracy     max |dTheta| / max |Theta| against the plain path and the oracle
   roofline     the coordinate-descent launch: algorithmic bytes per launch over
-               its CUDA-event duration, against the measured HBM copy bandwidth
+               its CUDA-event duration, against the measured HBM copy bandwidth;
+               sweep_model gives the bytes of the row-synchronous G schedule
   cpu_baseline the FP64 oracle on the host cores, on a bounded sample
   latency      p50 / p99 of the per-solve device time
   clocks       SM clocks and throttle reasons sampled during the timed region
 
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on the same workload and prints its line with "impl": "reference".
+--workload names another measurement: a single fit of synth.WORKLOADS (for
+example hub_p10000_n500_mixed), batch256, serve, regression, table4 or
+residual.
 """
 from __future__ import annotations
 
@@ -44,10 +52,11 @@ N_DATASETS = 10
 # the headline batched path: split-BF16 Gram on the tensor cores, CD in FP32,
 # sigma / convergence / Theta in FP64
 BATCH_PREC = "mixed"
-# per batched step: split/transpose, tcgen05 Gram, prep_diag, prep_matrix, column
-# order, lazy cd, eager cd queue, Theta zeroing (side stream), theta (the FP32
-# path has one SIMT Gram launch instead of two)
-KERNELS_PER_SOLVE = {"mixed": 9, "fp32": 8}
+# per batched step: coefficient-row and Theta zeroing (side stream), split/transpose,
+# tcgen05 Gram, prep_diag, prep_matrix, column order, lazy cd, eager cd queue,
+# theta (the FP32 path has one SIMT Gram launch instead of the split and the
+# tcgen05 Gram)
+KERNELS_PER_SOLVE = {"mixed": 10, "fp32": 9}
 
 
 def _env_rank():
