@@ -203,11 +203,17 @@ def run_reference(args):
 
 
 def _sha_of(paths):
+    """sha256 of the sources with comments and whitespace removed, so that a
+    profile stays attached to the code it measured across comment edits."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -552,8 +552,9 @@ __device__ void solve_column(int j, T* __restrict__ g, T* __restrict__ b, int* _
 // ===========================================================================
 // Lazy-gradient column solver.
 //
-// Same iterates as solve_column (Algorithm 1, ascending cyclic order), but
-// the gradient g = S_.j - S b is never stored.  The warp keeps only the
+// Algorithm 1 in ascending cyclic order, with an active-set phase before each
+// certifying sweep (see solve_column_lazy), and the gradient g = S_.j - S b
+// never stored.  The warp keeps only the
 // support of b_j, sorted by coordinate, in shared memory.  Each 128-coordinate
 // chunk forms its slice of g from coalesced 16-byte reads of row j and of the
 // rows of the support (S symmetric), so the chunk's reads are independent and
