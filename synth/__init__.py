@@ -16,8 +16,9 @@ the workload definitions used for measurement):
 For er and hub the diagonal starts at 1, is shifted so that the smallest
 eigenvalue is at least 0.1, and Theta is rescaled to unit diagonal.
 
-Sampling: Theta = L L' (Cholesky), X = Z L^{-T} with Z iid N(0, 1), so that
-Cov(x) = (L L')^{-1} = Theta^{-1}.  All randomness comes from
+Sampling: Theta = L L' (lower Cholesky factor L); each row is x = L^{-T} z with
+z iid N(0, 1), i.e. X = Z L^{-1}, so that Cov(x) = L^{-T} L^{-1} =
+(L L')^{-1} = Theta^{-1}.  All randomness comes from
 numpy.random.default_rng(seed) (PCG64), which is reproducible across
 platforms.
 """
@@ -207,8 +208,8 @@ def sample_x(theta: np.ndarray, n: int, rng: np.random.Generator,
     import scipy.linalg as sla
     L = np.linalg.cholesky(theta)
     Z = rng.standard_normal((n, theta.shape[0]))
-    # X = Z L^{-T}  <=>  L X' = Z'
-    Xt = sla.solve_triangular(L, Z.T, lower=True)
+    # x = L^{-T} z  <=>  L' X' = Z'  (L' upper triangular)
+    Xt = sla.solve_triangular(L.T, Z.T, lower=False)
     return np.ascontiguousarray(Xt.T).astype(dtype)
 
 
