@@ -98,3 +98,22 @@ def test_measures_limits():
     assert z["sen"] == 0.0 and z["spe"] == 1.0
     assert math.isnan(z["fdr"]) and math.isnan(z["mcc"])
     assert z["misr"] == pytest.approx(19 / 190)
+
+
+def test_measures_match_a_vectorised_count():
+    """oracle.support_metrics (plain loops) against the same measures counted
+    with whole-array operations, on random sparse pairs."""
+    rng = np.random.default_rng(9)
+    for p in (5, 40, 123):
+        A = np.where(rng.random((p, p)) < 0.15, rng.standard_normal((p, p)), 0.0)
+        B = np.where(rng.random((p, p)) < 0.15, rng.standard_normal((p, p)), 0.0)
+        A[:3] = B[:3]
+        m = oracle.support_metrics(A, B)
+        iu = np.triu_indices(p, 1)
+        e, t = A[iu] != 0, B[iu] != 0
+        tp, fp = int(np.sum(e & t)), int(np.sum(e & ~t))
+        tn, fn = int(np.sum(~e & ~t)), int(np.sum(~e & t))
+        assert (m["tp"], m["fp"], m["tn"], m["fn"]) == (tp, fp, tn, fn)
+        assert m["frobenius"] == pytest.approx(np.linalg.norm(A - B), rel=1e-12)
+        assert m["mcc"] == pytest.approx(
+            (tp * tn - fp * fn) / math.sqrt((tp + fp) * (tp + fn) * (tn + fp) * (tn + fn)), rel=1e-12)
