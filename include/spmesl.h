@@ -74,11 +74,13 @@ typedef enum {
     SPMESL_INNER_COLUMN = 1     /* per column ||b_next - b_cur||_inf (Algorithms 1-2) */
 } spmesl_inner_rule;
 
-/* How the per-column rule keeps g_j = S_.j - S b_j during a sweep.  Both give
- * the iterates of Algorithm 1; they differ in memory use only. */
+/* How the per-column rule keeps g_j = S_.j - S b_j during a sweep.  Both solve
+ * Algorithm 1's column problems to the same tolerance.  The lazy solver also
+ * sweeps each column's support alone before every certifying sweep, so its
+ * iterates take another path to the same solution. */
 typedef enum {
     SPMESL_GRADIENT_AUTO = 0,   /* lazy, with the eager solver for columns whose support
-                                   outgrows the lazy solver's list (512 entries) */
+                                   outgrows the lazy solver's list (256 entries) */
     SPMESL_GRADIENT_EAGER = 1,  /* g_j and b_j stored in shared memory, rank-1 update of the
                                    whole g_j after every coordinate move */
     SPMESL_GRADIENT_LAZY = 2    /* only the support of b_j stored; each 128-coordinate slice of
@@ -127,14 +129,16 @@ typedef struct {
                                    block of S is held in shared memory) */
 } spmesl_stats;
 
-/* Fill `opts` with the defaults: FP32, standardize = 1, center = 0,
+/* A helper (no passage of the paper): fill `opts` with the defaults: FP32,
+ * standardize = 1, center = 0,
  * lambda_rule = GIVEN, inner_rule = COLUMN, warps_per_block = 0. */
 void spmesl_default_opts(spmesl_opts* opts);
 
-/* Static text for a status code. */
+/* A helper (no passage of the paper): static text for a status code. */
 const char* spmesl_status_string(int status);
 
-/* Library ABI version (major * 10000 + minor * 100 + patch). */
+/* A helper (no passage of the paper): library ABI version
+ * (major * 10000 + minor * 100 + patch). */
 int spmesl_version(void);
 
 /* Penalty level for a rule (host computation; Section 2.1, Eqs. (10)-(11),
@@ -234,7 +238,8 @@ spmesl_status spmesl_fit_noalloc(const void* S, int n, int p, double lambda0, do
                                  int maxit, const spmesl_opts* opts, double* Theta, double* sigma,
                                  spmesl_stats* stats, void* stream);
 
-/* Synchronise `stream` and read the status and counters of the last fit that
+/* The fit's outcome (Algorithm 2): synchronise `stream` and read the status
+ * and counters of the last fit that
  * ran in `workspace` (p and precision as given to spmesl_fit).  Returns the
  * fit's status. */
 spmesl_status spmesl_fit_result(const void* workspace, int p, int precision,
@@ -279,7 +284,8 @@ spmesl_status spmesl_fit_residual(const void* X, int n, int p, int ldx, double l
                                   double* sigma, spmesl_stats* stats, void* workspace,
                                   size_t ws_bytes, void* stream);
 
-/* Copy the coefficients of the last fit in `workspace` to B (p x p FP64
+/* The regression coefficients of Eq. (5) (b_j of each column problem,
+ * Algorithm 2): copy the coefficients of the last fit in `workspace` to B (p x p FP64
  * device buffer, original scale, B[j*p + k] = b_jk, zero diagonal). */
 spmesl_status spmesl_fit_coefficients(const void* workspace, int p, int precision, double* B,
                                       void* stream);
@@ -348,7 +354,8 @@ spmesl_status spmesl_support_metrics(const double* Theta_hat, const double* Thet
                                      void* stream);
 
 /*
- * End-to-end solve from HOST data: copies X_host to the device, builds S
+ * End-to-end solve from HOST data (Section 2.2 and Algorithm 2): copies X_host
+ * to the device, builds S
  * (spmesl_gram), fits (spmesl_fit), copies Theta and sigma back to the host
  * buffers and synchronises `stream`.
  *   X_host      n x p row-major host buffer (FP64 for SPMESL_FP64, else FP32);
@@ -389,7 +396,8 @@ typedef struct {
 
 typedef struct spmesl_batch spmesl_batch;
 
-/* Plan a batch (host only: sizes, ordering, workspace layout).  The problems
+/* Plan a batch of Algorithm 2 fits (host only: sizes, ordering, workspace
+ * layout).  The problems
  * are copied; tol and maxit apply to every fit.  opts: precision FP64, FP32 or
  * MIXED (FP32 data; the Gram of every fit given as X runs as split-BF16
  * products on the tensor cores in one launch for the whole batch, the rest as
@@ -402,10 +410,12 @@ typedef struct spmesl_batch spmesl_batch;
 spmesl_status spmesl_batch_create(const spmesl_problem* problems, int count, double tol,
                                   int maxit, const spmesl_opts* opts, spmesl_batch** batch);
 
-/* Device workspace the batch needs (256-byte aligned when passed). */
+/* Device workspace of a batch of Algorithm 2 fits (256-byte aligned when
+ * passed). */
 size_t spmesl_batch_workspace_bytes(const spmesl_batch* batch);
 
-/* Enqueue the whole batch on `stream`: descriptor upload, Gram (fits with X),
+/* Enqueue the whole batch on `stream` (Section 2.2 and Algorithm 2 per fit):
+ * descriptor upload, Gram (fits with X),
  * standardisation, coordinate descent, Theta.  Asynchronous.  With use_graph
  * the sequence is captured into a CUDA graph on the first run (per
  * workspace) and replayed afterwards.  The workspace must not be reused until
@@ -413,19 +423,22 @@ size_t spmesl_batch_workspace_bytes(const spmesl_batch* batch);
 spmesl_status spmesl_batch_run(spmesl_batch* batch, void* workspace, size_t ws_bytes,
                                void* stream);
 
-/* Synchronise `stream`, write each fit's status to statuses[i] (host array in
+/* The batch's outcome (Algorithm 2 per fit): synchronise `stream`, write
+ * each fit's status to statuses[i] (host array in
  * the caller's problem order, may be NULL) and aggregate counters to stats
  * (may be NULL).  Returns the most severe status. */
 spmesl_status spmesl_batch_result(const spmesl_batch* batch, const void* workspace,
                                   int32_t* statuses, spmesl_stats* stats, void* stream);
 
-/* Autotune warps per block of the batch's coordinate-descent launch by timing
+/* Autotune (not in the paper) warps per block of the batch's
+ * coordinate-descent launch (Algorithm 1 per column) by timing
  * a few candidates on this workspace (runs the batch several times); the
  * choice is kept in the batch and written to *best_warps. */
 spmesl_status spmesl_batch_tune(spmesl_batch* batch, void* workspace, size_t ws_bytes,
                                 void* stream, int* best_warps);
 
-/* Release the batch's host resources (pinned staging, captured graph). */
+/* A helper (no passage of the paper): release the batch's host resources
+ * (pinned staging, captured graph). */
 void spmesl_batch_destroy(spmesl_batch* batch);
 
 /*

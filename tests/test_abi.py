@@ -147,3 +147,22 @@ def test_residual_invalid_arguments_rejected_on_host():
     bad_prec = sp.spmesl_default_opts()
     bad_prec.precision = 9
     assert call(opts=bad_prec) == sp.SPMESL_EINVAL
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each function's comment block in include/spmesl.h (the text since the
+    previous declaration) cites the paper's passage for the operation, or
+    states that the paper has no counterpart."""
+    cite = re.compile(r"Section|Eqs?\.|Algorithm|Proposition|Table|Theorem|"
+                      r"no passage of the paper|paper has no|not in the paper|has no serving")
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        decl = re.compile(r"^(?:spmesl_status|size_t|int|double|void|const char\*)\s+(spmesl_\w+)\s*\(",
+                          re.M)
+        prev, last = 0, ""
+        for m in decl.finditer(text):
+            block = text[prev:m.start()]
+            if not block.strip():         # declared right after another: shares its comment
+                block = last
+            assert cite.search(block), m.group(1)
+            prev, last = text.index(";", m.end()) + 1, block
