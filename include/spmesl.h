@@ -101,7 +101,10 @@ typedef struct {
     int32_t use_graph;          /* spmesl_batch_run: capture the batch's launches once into a
                                    CUDA graph and replay it on later runs */
     int32_t gradient;           /* spmesl_gradient: how a column keeps its gradient (column rule) */
-    int32_t reserved[7];
+    int32_t diagnostics;        /* 1: after the fit, one more launch checks every column's
+                                   (b_j, sigma_j) in FP64 on the device and fills kkt_viol,
+                                   dual_gap and err_est of spmesl_stats (0: not computed) */
+    int32_t reserved[6];
 } spmesl_opts;
 
 typedef struct {
@@ -127,6 +130,18 @@ typedef struct {
     int64_t active_sweeps;      /* sum over columns of sweeps over the support only (lazy solver) */
     int64_t active_moves;       /* coordinate updates in those sweeps (no S-row read: the support's
                                    block of S is held in shared memory) */
+    int32_t block_columns;      /* columns solved by the block solver (heavy columns and those the
+                                   lazy solver handed over; SPMESL_GRADIENT_AUTO / LAZY) */
+    int32_t diagnostics;        /* 1 when the three fields below were computed (opts.diagnostics) */
+    double kkt_viol;            /* largest violation of the lasso subgradient conditions of any
+                                   column, relative to its penalty lambda0 sigma_j, in FP64 on the
+                                   working matrix (Section 2.1; Algorithm 1's fixed point) */
+    double dual_gap;            /* largest relative duality gap (P - D) / P of any column's lasso
+                                   subproblem at its final sigma, in FP64 on the working matrix */
+    double err_est;             /* estimated max |dTheta| / max |Theta| of the result against the
+                                   exact estimator: the first-order effect of the measured
+                                   gradient residuals and sigma fixed-point residuals, plus the
+                                   rounding bound of the working matrix (see spmesl_opts) */
 } spmesl_stats;
 
 /* A helper (no passage of the paper): fill `opts` with the defaults: FP32,
@@ -220,19 +235,21 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
  * allocation after start-up).
  *   Arguments, outputs and device-side status are those of spmesl_fit, except
  *   that there is no workspace: the fit's scratch is one 64 MiB __device__
- *   array inside the library, held by every GPU that loads the library until
- *   the process exits.  record_phase_times is ignored.
- *   Size limit: the fit's scratch must fit in 64 MiB, i.e. p <= 2358 for
+ *   array inside the library.  record_phase_times is ignored.
+ *   The first call on each device (with that device current) looks up the
+ *   array's device address; that lookup loads the library's module, which
+ *   commits the 64 MiB on the device, and the device holds it until the
+ *   process exits.  Make that first call at start-up, and before any stream
+ *   capture.  If the device has no room for the array, SPMESL_ENOMEM.
+ *   Size limit: the fit's scratch must fit in 64 MiB, i.e. p <= 2352 for
  *   SPMESL_FP32 / SPMESL_MIXED and p <= 1664 for SPMESL_FP64; larger p returns
  *   SPMESL_ENOMEM before any work is enqueued.
- *   The first call on each device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
  *   All calls share the array and it keeps the last call's contents (each fit
  *   clears what must start at zero).  Calls whose work overlaps on the GPU
  *   race on the array: issue them on one stream or order them.
  *   stats non-NULL synchronises `stream` and fills everything except the
- *   timing fields.  No cudaMalloc, cudaFree or allocating library routine is
- *   called.
+ *   timing fields (lambda0 included).  No cudaMalloc, cudaFree or allocating
+ *   library routine is called.
  */
 spmesl_status spmesl_fit_noalloc(const void* S, int n, int p, double lambda0, double tol,
                                  int maxit, const spmesl_opts* opts, double* Theta, double* sigma,

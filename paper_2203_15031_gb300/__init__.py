@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("center", ctypes.c_int32), ("lambda_rule", ctypes.c_int32),
                 ("inner_rule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("record_phase_times", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("gradient", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("gradient", ctypes.c_int32), ("diagnostics", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Problem(ctypes.Structure):
@@ -71,7 +72,9 @@ class Stats(ctypes.Structure):
                 ("max_col_outer", ctypes.c_int32), ("ms_queue", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("batch_size", ctypes.c_int32),
                 ("reserved32", ctypes.c_int32), ("active_sweeps", ctypes.c_int64),
-                ("active_moves", ctypes.c_int64)]
+                ("active_moves", ctypes.c_int64), ("block_columns", ctypes.c_int32),
+                ("diagnostics", ctypes.c_int32), ("kkt_viol", ctypes.c_double),
+                ("dual_gap", ctypes.c_double), ("err_est", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}

@@ -429,6 +429,7 @@ spmesl_status spmesl_fit_result(const void* workspace, int p, int precision, spm
         stats->max_db = md;
         stats->max_col_sweeps = c.max_col_sweeps;
         stats->max_col_outer = c.outer_max;
+        stats->block_columns = c.block_cols;
         read_phase_times(workspace, stats);
     }
     return s;

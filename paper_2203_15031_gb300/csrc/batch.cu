@@ -44,6 +44,7 @@ struct BatchFit {
     FitCtrl* ctrl;
     void* XhT;            // split-BF16 operands (SPMESL_MIXED with X)
     void* XlT;
+    float* cmax;          // first-sweep chunk maxima of the lazy solver (standardised fits)
     double lambda0;
     int n, p, ldp;
     int col_start, gram_start, theta_start;
@@ -54,10 +55,12 @@ struct BatchFit {
 thread_local bool g_batch_pageable_staging = false;
 
 struct BatchHeader {
-    int next_col;         // column queue of the first coordinate-descent launch
-    int ovf_count;        // columns handed from the lazy to the eager kernel
-    int ovf_next;         // eager kernel's position in that queue
-    int pad[61];
+    int next_col;         // column queue of the lazy launch
+    int ovf_count;        // columns handed from the lazy kernel to the block solver
+    int ovf_next;         // block solver's position in that queue
+    int n_heavy;          // heavy columns: the first n_heavy of the heat order
+    int heavy_next;       // block solver's position among them
+    int pad[59];
 };
 
 // Largest f with prefix[f] <= idx (prefix ascending, prefix[0] = 0).
@@ -135,7 +138,7 @@ __global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits, int*
         bad |= standardize_row<T>(static_cast<const T*>(f.S), f.p, f.ldp, r, f.cs, f.csf,
                                   static_cast<T*>(f.SC), nullptr, nullptr,
                                   static_cast<T*>(f.diag), threadIdx.x, blockDim.x,
-                                  (T)f.lambda0, heat ? &cnt : nullptr);
+                                  (T)f.lambda0, heat ? &cnt : nullptr, f.cmax);
         if (cnt) atomicAdd(&heat[f.col_start + r], cnt);
     }
     if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
@@ -144,7 +147,8 @@ __global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits, int*
 
 
 template <typename T>
-__device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, int maxit) {
+__device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, int maxit,
+                                                 int ovf_supp = LAZY_CAP) {
     CDArgs<T> a;
     a.SC = static_cast<const T*>(f.SC);
     a.BT = static_cast<T*>(f.BT);
@@ -163,6 +167,8 @@ __device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, 
     a.ovf_count = nullptr;
     a.order = nullptr;
     a.n_queue = f.p;
+    a.ovf_supp = ovf_supp;
+    a.chunk_max = f.cmax;
     return a;
 }
 
@@ -205,9 +211,11 @@ __global__ void __launch_bounds__(512) batch_cd_kernel(const BatchFit* __restric
     }
 }
 
-// Lazy gradient over all columns of all fits; overflowing columns are queued.
+// Lazy gradient over all columns of all fits; overflowing columns are queued
+// for the block solver, and the first n_heavy columns of the heat order
+// belong to it from the start.
 // At most 8 warps a block and 3 blocks an SM: the kernel then keeps its
-// working set in registers (79) instead of spilling inside the sweep.
+// working set in registers instead of spilling inside the sweep.
 constexpr int LAZY_MAX_WARPS = 8;
 template <typename T, bool STD>
 __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(const BatchFit* __restrict__ fits,
@@ -215,15 +223,17 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
                                                             int count, int total_cols, int max_ldp,
                                                             double tol, int maxit,
                                                             BatchHeader* hdr, int* ovf_list,
-                                                            const int* __restrict__ order) {
+                                                            const int* __restrict__ order,
+                                                            int ovf_supp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)warp * lazy_warp_smem_bytes<T>(max_ldp);
+    const int q0 = order ? *reinterpret_cast<volatile int*>(&hdr->n_heavy) : 0;
     for (;;) {
         int gc = 0;
         if (lane == 0) {
-            gc = atomicAdd(&hdr->next_col, 1);
+            gc = q0 + atomicAdd(&hdr->next_col, 1);
             if (order && gc < total_cols) gc = order[gc];
         }
         gc = __shfl_sync(FULL_MASK, gc, 0);
@@ -231,12 +241,46 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
         const int fi = find_fit(col_prefix, count, gc);
         const BatchFit& f = fits[fi];
         if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) continue;
-        const CDArgs<T> a = column_args<T>(f, tol, maxit);
+        const CDArgs<T> a = column_args<T>(f, tol, maxit, ovf_supp);
         ColCounters cnt;
         if (!solve_column_lazy<T, STD>(gc - f.col_start, wsm, a, cnt) && lane == 0)
             ovf_list[atomicAdd(&hdr->ovf_count, 1)] = gc;
         __syncwarp();
         flush_counters(f.ctrl, cnt);
+    }
+}
+
+// Block solver over the heavy columns at the head of the heat order
+// (from_overflow = 0, beside the lazy launch) or over the columns the lazy
+// launch handed over (from_overflow = 1, after it); one block per column.
+template <typename T, bool STD>
+__global__ void __launch_bounds__(BLK_THREADS) batch_cd_block_kernel(const BatchFit* __restrict__ fits,
+                                                                     const int* __restrict__ col_prefix,
+                                                                     int count, double tol, int maxit,
+                                                                     BatchHeader* hdr,
+                                                                     const int* __restrict__ queue,
+                                                                     int from_overflow) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockScratch sc;
+    const int nq = from_overflow ? *reinterpret_cast<volatile int*>(&hdr->ovf_count)
+                                 : *reinterpret_cast<volatile int*>(&hdr->n_heavy);
+    int* next = from_overflow ? &hdr->ovf_next : &hdr->heavy_next;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(next, 1);
+            sc.col = t < nq ? queue[t] : -1;
+        }
+        __syncthreads();
+        const int gc = sc.col;
+        __syncthreads();
+        if (gc < 0) break;
+        const int fi = find_fit(col_prefix, count, gc);
+        const BatchFit& f = fits[fi];
+        if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) continue;
+        const CDArgs<T> a = column_args<T>(f, tol, maxit);
+        ColCounters cnt;
+        solve_column_block<T, STD>(gc - f.col_start, smem_raw, a, cnt, sc);
+        flush_counters_block(f.ctrl, cnt);
     }
 }
 
@@ -290,7 +334,8 @@ struct FitPlan {
     const void* S;
     double* Theta;
     double* sigma;
-    size_t off_ctrl, off_cs, off_csf, off_sigma, off_status, off_diag, off_mu, off_Sg, off_SC, off_BT;
+    size_t off_ctrl, off_cs, off_csf, off_sigma, off_status, off_diag, off_cmax, off_mu, off_Sg, off_SC,
+        off_BT;
     size_t off_XhT, off_XlT;
     int col_start, gram_start, theta_start, split_start;
 };
@@ -353,6 +398,9 @@ struct spmesl_batch {
     // side stream that zeroes Theta under the coordinate-descent launch
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, join_bt = nullptr;
+    // second side stream: the block solver's launch over the heavy columns
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t fork2 = nullptr, join2 = nullptr;
     // record_phase_times (runs without a graph): events around the CD launch
     int record_phase_times = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -403,15 +451,20 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
                                                                                    b->standardize);
     // rows per fit spread over blocks; enough blocks overall to fill the GPU
     const int mx = std::max(1, std::min(b->max_p, (num_sms() * 8 + count - 1) / count));
-    // column order for the lazy launch (standardised working matrix only)
+    // column order for the lazy launch (standardised working matrix only);
+    // with AUTO the heavy columns lead it and go to the block solver
     const bool lazy_order = b->gradient != SPMESL_GRADIENT_EAGER && b->standardize;
+    const bool route = b->gradient == SPMESL_GRADIENT_AUTO;
+    const bool heavy = route && lazy_order;
     int* heat = reinterpret_cast<int*>(ws + b->off_heat);
     int* order = reinterpret_cast<int*>(ws + b->off_order);
     if (lazy_order &&
         (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)b->total_cols, st)) != cudaSuccess)
         return e;
     batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits, lazy_order ? heat : nullptr);
-    if (lazy_order) order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, b->total_cols, order);
+    if (lazy_order)
+        order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, b->total_cols, order,
+                                                 heavy ? &hdr->n_heavy : nullptr);
 
     const size_t budget = (size_t)max_smem_block() - 1024;
     const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
@@ -420,6 +473,27 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     const bool timed = b->record_phase_times && b->ev[0];
     if (timed) cudaEventRecord(b->ev[0], st);
     if (lazy) {
+        // block solver: persistent grid, one block per column
+        auto bk = b->standardize ? batch_cd_block_kernel<T, true> : batch_cd_block_kernel<T, false>;
+        const size_t bsm = block_smem_bytes<T>(b->max_ldp);
+        if (bsm > budget) return cudaErrorInvalidValue;
+        if ((e = cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bsm)) != cudaSuccess)
+            return e;
+        int bper_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bper_sm, bk, BLK_THREADS, bsm)) !=
+            cudaSuccess)
+            return e;
+        const int bgrid = num_sms() * std::max(1, std::min(bper_sm, 2));
+        if (heavy) {
+            // the heavy columns start first, on the second side stream, beside the lazy launch
+            if ((e = cudaEventRecord(b->fork2, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(b->side2, b->fork2, 0)) != cudaSuccess)
+                return e;
+            bk<<<bgrid, BLK_THREADS, bsm, b->side2>>>(fits, colp, count, b->tol, b->maxit, hdr,
+                                                      order, 0);
+            if ((e = cudaEventRecord(b->join2, b->side2)) != cudaSuccess) return e;
+        }
         // W (tuned) shapes the lazy launch, which does almost all the work
         const size_t lper = lazy_warp_smem_bytes<T>(b->max_ldp);
         const int LW = std::max(1, std::min({W, LAZY_MAX_WARPS, (int)(budget / lper)}));
@@ -435,27 +509,31 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
         lper_sm = std::max(lper_sm, 1);
         const int lgrid = std::min((b->total_cols + LW - 1) / LW, num_sms() * lper_sm);
         lk<<<lgrid, 32 * LW, lsm, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
-                                        b->maxit, hdr, ovf, lazy_order ? order : nullptr);
+                                        b->maxit, hdr, ovf, lazy_order ? order : nullptr,
+                                        route ? ACT_MAX : LAZY_CAP);
+        // the columns the lazy launch handed over
+        bk<<<bgrid, BLK_THREADS, bsm, st>>>(fits, colp, count, b->tol, b->maxit, hdr, ovf, 1);
+        if (heavy && (e = cudaStreamWaitEvent(st, b->join2, 0)) != cudaSuccess) return e;
+    } else {
+        // eager gradient for every column
+        const size_t per_warp = warp_smem_bytes<T>(b->max_ldp);
+        const int wmax = (int)std::min<size_t>(16, budget / per_warp);
+        if (wmax < 1) return cudaErrorInvalidValue;
+        const int EW = std::max(1, std::min(W, wmax));
+        const size_t smem = per_warp * EW;
+        auto kern = b->standardize ? batch_cd_kernel<T, true> : batch_cd_kernel<T, false>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * EW, smem)) !=
+            cudaSuccess)
+            return e;
+        per_sm = std::max(per_sm, 1);
+        const int grid = std::min((b->total_cols + EW - 1) / EW, num_sms() * per_sm);
+        kern<<<grid, 32 * EW, smem, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
+                                          b->maxit, hdr, ovf, 0);
     }
-    // eager launch: every column, or only the queue the lazy launch left
-    const size_t per_warp = warp_smem_bytes<T>(b->max_ldp);
-    const int wmax = (int)std::min<size_t>(16, budget / per_warp);
-    if (wmax < 1) return cudaErrorInvalidValue;
-    int EW = lazy ? (int)std::max<size_t>(1, (budget / 2) / per_warp) : W;
-    EW = std::max(1, std::min(EW, wmax));
-    const size_t smem = per_warp * EW;
-    auto kern = b->standardize ? batch_cd_kernel<T, true> : batch_cd_kernel<T, false>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * EW, smem)) !=
-        cudaSuccess)
-        return e;
-    per_sm = std::max(per_sm, 1);
-    const int grid = std::min((b->total_cols + EW - 1) / EW, num_sms() * per_sm);
-    kern<<<grid, 32 * EW, smem, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
-                                      b->maxit, hdr, ovf, lazy ? 1 : 0);
     if (timed) cudaEventRecord(b->ev[1], st);
     if ((e = cudaStreamWaitEvent(st, b->join, 0)) != cudaSuccess) return e;   // join
     batch_theta_kernel<T><<<b->total_theta, dim3(32, 8), 0, st>>>(fits, thetap, count);
@@ -494,6 +572,9 @@ bool stage_table(spmesl_batch* b, unsigned char* ws) {
         d.SC = ws + f.off_SC;
         d.BT = ws + f.off_BT;
         d.diag = ws + f.off_diag;
+        // first-sweep chunk maxima: the lazy solver on the standardised matrix
+        d.cmax = (b->gradient != SPMESL_GRADIENT_EAGER && b->standardize)
+                     ? reinterpret_cast<float*>(ws + f.off_cmax) : nullptr;
         d.cs = reinterpret_cast<double*>(ws + f.off_cs);
         d.csf = reinterpret_cast<float*>(ws + f.off_csf);
         d.sigma = reinterpret_cast<double*>(ws + f.off_sigma);
@@ -626,6 +707,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
         f.off_sigma = off;  off += align_up((size_t)f.p * 8, 256);
         f.off_status = off; off += align_up((size_t)f.p * 4, 256);
         f.off_diag = off;   off += align_up((size_t)f.p * s, 256);
+        f.off_cmax = off;   off += align_up((size_t)f.p * row_chunks(f.ldp) * 4, 256);
         if (q.X) {
             f.off_mu = off;  off += align_up((size_t)f.p * s, 256);
             f.off_Sg = off;  off += align_up((size_t)f.p * f.p * s, 256);
@@ -705,7 +787,10 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
         if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->join_bt, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&b->join_bt, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&b->side2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join2, cudaEventDisableTiming) != cudaSuccess)
             return SPMESL_ECUDA;
     }
     auto enqueue = [&](cudaStream_t s2) {
@@ -779,6 +864,7 @@ spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, 
         agg.n_degenerate += c.n_degenerate;
         agg.max_col_sweeps = std::max(agg.max_col_sweeps, c.max_col_sweeps);
         agg.max_col_outer = std::max(agg.max_col_outer, c.outer_max);
+        agg.block_columns += c.block_cols;
     }
     agg.status = worst;
     if (b->ev_recorded) {
@@ -840,6 +926,9 @@ void spmesl_batch_destroy(spmesl_batch* b) {
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->join) cudaEventDestroy(b->join);
     if (b->join_bt) cudaEventDestroy(b->join_bt);
+    if (b->side2) cudaStreamDestroy(b->side2);
+    if (b->fork2) cudaEventDestroy(b->fork2);
+    if (b->join2) cudaEventDestroy(b->join2);
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
     if (b->ev[1]) cudaEventDestroy(b->ev[1]);
     if (b->pinned) {

@@ -71,11 +71,13 @@ __global__ void __launch_bounds__(512) cd_column_lazy_kernel(CDArgs<T> a) {
     unsigned char* wsm = smem_raw + (size_t)warp * lazy_warp_smem_bytes<T>(a.ldp);
     FitCtrl* ctrl = a.ctrl;
     if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
+    // the first n_heavy columns of the order belong to the block solver
+    const int q0 = *reinterpret_cast<volatile int*>(&ctrl->n_heavy);
     ColCounters cnt;
     for (;;) {
         int j = 0;
         if (lane == 0) {
-            const int q = atomicAdd(&ctrl->next_col, 1);
+            const int q = q0 + atomicAdd(&ctrl->next_col, 1);
             j = q >= a.n_queue ? a.p : (a.order ? a.order[q] : q);
         }
         j = __shfl_sync(FULL_MASK, j, 0);
@@ -85,6 +87,35 @@ __global__ void __launch_bounds__(512) cd_column_lazy_kernel(CDArgs<T> a) {
         __syncwarp();
     }
     flush_counters(ctrl, cnt);
+}
+
+// Block solver (one block per column, see solve_column_block): the heavy
+// columns at the head of the heat order (from_overflow = 0, launched beside
+// the lazy kernel) or the columns the lazy solver handed over (from_overflow
+// = 1, after it).
+template <typename T, bool STD>
+__global__ void __launch_bounds__(BLK_THREADS) cd_column_block_kernel(CDArgs<T> a,
+                                                                      int from_overflow) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockScratch sc;
+    FitCtrl* ctrl = a.ctrl;
+    if (*reinterpret_cast<volatile int*>(&ctrl->err) != 0) return;
+    const int nq = from_overflow ? *reinterpret_cast<volatile int*>(a.ovf_count)
+                                 : *reinterpret_cast<volatile int*>(&ctrl->n_heavy);
+    int* next = from_overflow ? &ctrl->ovf_next : &ctrl->heavy_next;
+    ColCounters cnt;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(next, 1);
+            sc.col = t < nq ? (from_overflow ? a.ovf_list[t] : a.order[t]) : -1;
+        }
+        __syncthreads();
+        const int j = sc.col;
+        __syncthreads();
+        if (j < 0) break;
+        solve_column_block<T, STD>(j, smem_raw, a, cnt, sc);
+    }
+    flush_counters_block(ctrl, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -295,12 +326,13 @@ __global__ void prep_diag_kernel(const T* __restrict__ S, int p, int standardize
 template <typename T>
 __global__ void prep_matrix_kernel(const T* __restrict__ S, int p, int ldp, const double* cs,
                                    const float* csf, T* SC, T* GT, T* diag, int init_g,
-                                   FitCtrl* ctrl, T heat_lam, int* heat) {
+                                   FitCtrl* ctrl, T heat_lam, int* heat, float* cmax) {
     bool bad = false;
     for (int r = blockIdx.x; r < p; r += gridDim.x) {
         int cnt = 0;
         bad |= standardize_row<T>(S, p, ldp, r, cs, csf, SC, init_g ? GT : nullptr, nullptr,
-                                  diag, threadIdx.x, blockDim.x, heat_lam, heat ? &cnt : nullptr);
+                                  diag, threadIdx.x, blockDim.x, heat_lam, heat ? &cnt : nullptr,
+                                  cmax);
         if (cnt) atomicAdd(&heat[r], cnt);
     }
     if (bad) set_error(ctrl, DEV_ERR_NONFINITE);
@@ -324,8 +356,10 @@ __global__ void theta_kernel(const T* __restrict__ BT, int p, int ldp,
 }
 
 // Zero n doubles (16-byte stores where aligned): Theta before the sparse
-// Theta kernel.
-__global__ void zero_kernel(double* __restrict__ x, size_t n) {
+// Theta kernel.  Does nothing when the fit reported a device-side error
+// (non-finite input): Theta is then left as the caller gave it.
+__global__ void zero_kernel(double* __restrict__ x, size_t n, const FitCtrl* ctrl) {
+    if (*reinterpret_cast<const volatile int*>(&ctrl->err) != 0) return;
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
@@ -400,16 +434,70 @@ static cudaError_t device_limits() {
 static size_t smem_budget() { return (size_t)g_max_smem_block - 1024; }
 
 int max_p_for(int precision) {
-    // one warp needs warp_smem_bytes(ldp) of shared memory; the opt-in block
-    // limit on GB300 is 227 KB.
+    // one warp of the eager solver needs warp_smem_bytes(ldp) of shared
+    // memory and one block of the block solver block_smem_bytes(ldp); the
+    // opt-in block limit on GB300 is 227 KB.
     const size_t budget = 232448 - 1024;
     int p = 32;
     if (precision == SPMESL_FP64) {
-        while (warp_smem_bytes<double>(p + 32) <= budget) p += 32;
+        while (warp_smem_bytes<double>(p + 32) <= budget && block_smem_bytes<double>(p + 32) <= budget)
+            p += 32;
     } else {
-        while (warp_smem_bytes<float>(p + 32) <= budget) p += 32;
+        while (warp_smem_bytes<float>(p + 32) <= budget && block_smem_bytes<float>(p + 32) <= budget)
+            p += 32;
     }
     return p;
+}
+
+// Side stream and fork/join events of the calling thread on the current
+// device, for the block solver's launch over the heavy columns beside the lazy
+// launch.  One set per thread and device, so the fork/join records of fits
+// issued from different threads cannot interleave; they live as long as the
+// process.
+namespace {
+struct SideRes {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxSideDevices = 64;
+}  // namespace
+
+static cudaError_t side_resources(SideRes** out) {
+    thread_local SideRes res[kMaxSideDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxSideDevices) return cudaErrorInvalidDevice;
+    SideRes& r = res[dev];
+    if (!r.s) {
+        if ((e = cudaStreamCreateWithFlags(&r.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming)) != cudaSuccess)
+            return e;
+    }
+    *out = &r;
+    return cudaSuccess;
+}
+
+// ctrl->n_heavy = 1 when the one column of a single regression is heavy.
+__global__ void heavy_flag_kernel(const int* __restrict__ heat, int* __restrict__ n_heavy) {
+    if (threadIdx.x == 0) *n_heavy = heat[0] > HEAVY_HEAT ? 1 : 0;
+}
+
+// Persistent grid of the block solver for this size.
+template <typename T, bool STD>
+static cudaError_t block_launch_shape(int ldp, size_t& smem, int& grid) {
+    auto bk = cd_column_block_kernel<T, STD>;
+    smem = block_smem_bytes<T>(ldp);
+    if (smem > smem_budget()) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bk, BLK_THREADS, smem)) !=
+        cudaSuccess)
+        return e;
+    grid = g_num_sms * std::max(1, std::min(per_sm, 2));
+    return cudaSuccess;
 }
 
 template <typename T, bool STD>
@@ -438,10 +526,17 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     a.ovf_count = &ctrl->ovf_count;
     a.order = nullptr;
     a.n_queue = f.p;
+    a.chunk_max = nullptr;
     const bool single = f.response_col >= 0;    // one regression: lazy column rule
     const bool joint = !single && f.inner_rule == SPMESL_INNER_JOINT;
     // Lazy launch shape (warps per block, blocks per SM).
     const bool lazy = single || (!joint && f.gradient != SPMESL_GRADIENT_EAGER);
+    // AUTO: heavy columns (heat above HEAVY_HEAT) go to the block solver beside
+    // the lazy launch, and the lazy solver hands over a column whose support
+    // outgrows its active-set phase; LAZY: the lazy solver keeps every column
+    // its list can hold.
+    const bool route = lazy && f.gradient == SPMESL_GRADIENT_AUTO;
+    a.ovf_supp = route ? ACT_MAX : LAZY_CAP;
     auto lk = cd_column_lazy_kernel<T, STD>;
     const size_t lper = lazy_warp_smem_bytes<T>(L.ldp);
     int LW = f.warps_per_block > 0 ? f.warps_per_block : 8;
@@ -457,15 +552,20 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
             return e;
         lper_sm = std::max(lper_sm, 1);
     }
-    // When there are more columns than resident warps, the lazy queue takes
-    // the columns heaviest first (standardised matrix).  The active index
-    // vectors are the joint rule's; the column rule lends them to the heat
-    // counts and the order.
-    const bool ordered = !single && lazy && f.standardize && f.p > g_num_sms * lper_sm * LW;
-    int* heat = ordered ? a.active_next : nullptr;
+    // The lazy queue takes the columns heaviest first (standardised matrix)
+    // when there are more columns than resident warps or when heavy columns
+    // are routed.  The active index vectors are the joint rule's; the column
+    // rule lends them to the heat counts and the order.
+    const bool heavy = route && f.standardize;
+    const bool ordered = !single && lazy && f.standardize &&
+                         (heavy || f.p > g_num_sms * lper_sm * LW);
+    int* heat = (ordered || (single && heavy)) ? a.active_next : nullptr;
+    // first-sweep chunk maxima (standardised lazy solves)
+    float* cmax = (lazy && f.standardize) ? reinterpret_cast<float*>(ws + L.cmax) : nullptr;
+    a.chunk_max = cmax;
 
     if ((e = cudaMemsetAsync(ctrl, 0, sizeof(FitCtrl), st)) != cudaSuccess) return e;
-    if (ordered && (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)f.p, st)) != cudaSuccess)
+    if (heat && (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)f.p, st)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(ws + L.BT, 0, (size_t)f.p * L.ldp * sizeof(T), st)) != cudaSuccess)
         return e;
@@ -478,16 +578,17 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
         prep_matrix_kernel<T><<<grid, pb, 0, st>>>(
             reinterpret_cast<const T*>(f.S), f.p, L.ldp, reinterpret_cast<double*>(ws + L.cs),
             reinterpret_cast<const float*>(ws + L.csf), reinterpret_cast<T*>(ws + L.SC), a.GT,
-            reinterpret_cast<T*>(ws + L.diag), joint ? 1 : 0, ctrl, (T)f.lambda0, heat);
+            reinterpret_cast<T*>(ws + L.diag), joint ? 1 : 0, ctrl, (T)f.lambda0, heat, cmax);
     }
     if (ordered) {
-        order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, f.p, a.active);
+        order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, f.p, a.active, heavy ? &ctrl->n_heavy : nullptr);
         a.order = a.active;
     }
     if (single) {
         // a queue of one column: active[j] = j after prep_diag_kernel
         a.order = a.active + f.response_col;
         a.n_queue = 1;
+        if (heavy) heavy_flag_kernel<<<1, 32, 0, st>>>(heat + f.response_col, &ctrl->n_heavy);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
@@ -509,6 +610,20 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     if (f.phase_events) cudaEventRecord(f.phase_events[0], st);
     if (!joint) {
         if (lazy) {
+            size_t bsm = 0;
+            int bgrid = 0;
+            if ((e = block_launch_shape<T, STD>(L.ldp, bsm, bgrid)) != cudaSuccess) return e;
+            auto bk = cd_column_block_kernel<T, STD>;
+            SideRes* side = nullptr;
+            if (heavy) {
+                // heavy columns on the block solver, beside the lazy launch
+                if ((e = side_resources(&side)) != cudaSuccess) return e;
+                if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess)
+                    return e;
+                bk<<<single ? 1 : bgrid, BLK_THREADS, bsm, side->s>>>(a, 0);
+                if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return e;
+            }
             // lazy gradient: small shared-memory footprint, many columns per SM
             if (single) {
                 lk<<<1, 32, lper, st>>>(a);          // one warp for the one column
@@ -516,19 +631,23 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
                 const int lgrid = std::min((f.p + LW - 1) / LW, g_num_sms * lper_sm);
                 lk<<<lgrid, 32 * LW, lsm, st>>>(a);
             }
+            // the columns the lazy solver handed over
+            bk<<<single ? 1 : bgrid, BLK_THREADS, bsm, st>>>(a, 1);
+            if (heavy && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
+        } else {
+            // eager gradient for every column
+            auto kern = cd_column_kernel<T, STD>;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+            int per_sm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) !=
+                cudaSuccess)
+                return e;
+            per_sm = auto_shape ? 1 : std::max(per_sm, 1);
+            const int grid = std::min((f.p + W - 1) / W, g_num_sms * per_sm);
+            kern<<<grid, threads, smem, st>>>(a, 0);
         }
-        // eager gradient: all columns, or only those the lazy solver handed over
-        auto kern = cd_column_kernel<T, STD>;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) !=
-            cudaSuccess)
-            return e;
-        per_sm = auto_shape ? 1 : std::max(per_sm, 1);
-        const int grid = std::min((f.p + W - 1) / W, g_num_sms * per_sm);
-        kern<<<grid, threads, smem, st>>>(a, lazy ? 1 : 0);
     } else {
         auto kern = cd_joint_kernel<T, STD>;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -555,7 +674,7 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
         if (f.phase_events) cudaEventRecord(f.phase_events[2], st);
         return cudaGetLastError();
     }
-    zero_kernel<<<g_num_sms * 4, 256, 0, st>>>(f.Theta, (size_t)f.p * f.p);
+    zero_kernel<<<g_num_sms * 4, 256, 0, st>>>(f.Theta, (size_t)f.p * f.p, ctrl);
     theta_kernel<T><<<theta_pairs<T>(f.p), dim3(32, 8), 0, st>>>(a.BT, f.p, L.ldp, a.sigma,
                                        reinterpret_cast<const double*>(ws + L.cs), f.Theta,
                                        f.sigma_out, ctrl);

@@ -2,6 +2,7 @@
 // Device building blocks of the coordinate-descent fit, shared by the single-fit
 // kernels (cd.cu) and the batched kernels (batch.cu).
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -22,10 +23,16 @@ struct CDArgs {
     FitCtrl* ctrl;
     int p, ldp, maxit;
     double lambda0, tol;
-    int* ovf_list;       // columns handed from the lazy solver to the eager one
+    int* ovf_list;       // columns handed from the lazy solver to the block (or eager) solver
     int* ovf_count;
     const int* order;    // queue order of the lazy solver (nullptr: 0..p-1)
     int n_queue;         // columns the lazy solver takes from its queue
+    int ovf_supp;        // the lazy solver hands a column over when its support exceeds this
+                         // at the start of an active-set phase (ACT_MAX with heavy-column
+                         // routing, LAZY_CAP without)
+    const float* chunk_max;   // per column j and 128-coordinate chunk c, max_k |S^C_jk| over
+                              // the chunk (k != j), written by the standardisation pass; the
+                              // first sweep's skip test starts from it (nullptr: scan all)
 };
 
 namespace {
@@ -33,10 +40,13 @@ namespace {
 // of off-diagonal standardised entries above lambda0, from standardize_row;
 // counting sort, one block), so the longest column solves start first instead
 // of in the tail of the launch.  Ties in any order: a column's result does not
-// depend on when it runs.
+// depend on when it runs.  With n_heavy, also the number of columns whose heat
+// exceeds HEAVY_HEAT: they lead the order and go to the block solver.
 constexpr int HEAT_BINS = 64;
+constexpr int HEAVY_HEAT = 32;
 __global__ void __launch_bounds__(1024) order_by_heat_kernel(const int* __restrict__ heat, int n,
-                                                          int* __restrict__ order) {
+                                                          int* __restrict__ order,
+                                                          int* __restrict__ n_heavy) {
     __shared__ int bin[HEAT_BINS];
     const int t = threadIdx.x;
     if (t < HEAT_BINS) bin[t] = 0;
@@ -49,6 +59,7 @@ __global__ void __launch_bounds__(1024) order_by_heat_kernel(const int* __restri
             const int c = bin[h];
             bin[h] = run;
             run += c;
+            if (h == HEAVY_HEAT + 1 && n_heavy) *n_heavy = run;
         }
     }
     __syncthreads();
@@ -341,11 +352,18 @@ __device__ double residual_quadratic_form(int j, const T* __restrict__ b, const 
     if (ns <= SUPP_CAP) {
         for (int t = lane; t < ns; t += 32) {
             const int k = list[t];
-            lin += (double)b[k] * (double)a.SC[(size_t)k * a.ldp + j];
+            lin = fma((double)b[k], (double)a.SC[(size_t)k * a.ldp + j], lin);
         }
-        for (int t = lane; t < ns * ns; t += 32) {
-            const int k = list[t / ns], l = list[t % ns];
-            quad += (double)b[k] * (double)b[l] * (double)a.SC[(size_t)k * a.ldp + l];
+        // rows of the support in turn, lanes over its columns (FP64 products)
+        for (int u = 0; u < ns; ++u) {
+            const int k = list[u];
+            const T* __restrict__ row = a.SC + (size_t)k * a.ldp;
+            double part = 0.0;
+            for (int v = lane; v < ns; v += 32) {
+                const int l = list[v];
+                part = fma((double)b[l], (double)row[l], part);
+            }
+            quad = fma((double)b[k], part, quad);
         }
         lin = warp_sum(lin);
         quad = warp_sum(quad);
@@ -379,63 +397,94 @@ __device__ double residual_quadratic_form(int j, const T* __restrict__ b, const 
 
 // Row r of S^C = C S C into SC (zero padding up to ldp), optionally copied
 // into GT, with BT's row cleared.  FP32 data is scaled in FP32 by the scales
-// rounded once to FP32 (csf); FP64 data in FP64.  Threads tid, tid + nthr, ...
-// of the row.  Returns true if a non-finite entry was seen.
+// rounded once to FP32 (csf); FP64 data in FP64.  One warp takes one
+// 128-coordinate chunk of the row at a time (threads tid, tid + nthr, ...;
+// nthr a multiple of 32).  Optional outputs: heat, this thread's count of
+// off-diagonal |SC_rc| > heat_lam; cmax, per chunk c of the row the largest
+// off-diagonal |SC_rk| (row r of a p x num_chunks(ldp) table; S^C is
+// symmetric, so it is also column r's first-sweep gradient bound).  Returns
+// true if a non-finite entry was seen.
 template <typename T>
 __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, int ldp, int r,
                                                 const double* __restrict__ cs,
                                                 const float* __restrict__ csf,
                                                 T* __restrict__ SC, T* __restrict__ GT,
                                                 T* __restrict__ BT, T* __restrict__ diag, int tid,
-                                                int nthr, T heat_lam = T(0), int* heat = nullptr) {
-    // heat (optional): this thread's count of off-diagonal |SC_rc| > heat_lam
+                                                int nthr, T heat_lam = T(0), int* heat = nullptr,
+                                                float* __restrict__ cmax = nullptr) {
     bool bad = false;
+    const int lane = tid & 31;
     const T cr = sizeof(T) == 4 ? (T)csf[r] : (T)cs[r];
     const T* __restrict__ srow = S + (size_t)r * p;
     T* __restrict__ out = SC + (size_t)r * ldp;
-    if constexpr (sizeof(T) == 4) {
-        // 16-byte accesses when the rows of S are 16-byte aligned (same arithmetic)
-        if ((p & 3) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0) {
-            const float4* __restrict__ s4 = reinterpret_cast<const float4*>(srow);
-            const float4* __restrict__ c4 = reinterpret_cast<const float4*>(csf);
-            float4* __restrict__ o4 = reinterpret_cast<float4*>(out);
-            float4* __restrict__ g4 = GT ? reinterpret_cast<float4*>(GT + (size_t)r * ldp) : nullptr;
-            float4* __restrict__ b4 = BT ? reinterpret_cast<float4*>(BT + (size_t)r * ldp) : nullptr;
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int q = tid; q < ldp / 4; q += nthr) {
-                float4 v = z;
-                if (4 * q < p) {                      // p % 4 == 0: the whole quad is inside
-                    const float4 s = s4[q], cc = c4[q];
-                    bad |= !isfinite(s.x) || !isfinite(s.y) || !isfinite(s.z) || !isfinite(s.w);
-                    v = make_float4(s.x * cr * cc.x, s.y * cr * cc.y, s.z * cr * cc.z,
-                                    s.w * cr * cc.w);
-                    const int d = r - 4 * q;
-                    if (d >= 0 && d < 4)
-                        diag[r] = d == 0 ? v.x : d == 1 ? v.y : d == 2 ? v.z : v.w;
-                    if (heat)
-                        *heat += (d != 0 && fabsf(v.x) > heat_lam) + (d != 1 && fabsf(v.y) > heat_lam) +
-                                 (d != 2 && fabsf(v.z) > heat_lam) + (d != 3 && fabsf(v.w) > heat_lam);
+    T* __restrict__ grow = GT ? GT + (size_t)r * ldp : nullptr;
+    T* __restrict__ brow = BT ? BT + (size_t)r * ldp : nullptr;
+    const int nch = num_chunks(ldp);
+    // 16-byte accesses when the rows of S are 16-byte aligned (same arithmetic)
+    const bool vec = sizeof(T) == 4 && (p & 3) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
+    for (int ch = tid >> 5; ch < nch; ch += nthr >> 5) {
+        const int c0 = ch * CHUNK;
+        float mx = 0.f;
+        if constexpr (sizeof(T) == 4) {
+            if (vec) {
+                const int c = c0 + 4 * lane;
+                if (c < ldp) {                        // ldp % 4 == 0: the quad is inside the row
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (c < p) {                      // p % 4 == 0: the whole quad is inside
+                        const float4 sv = *reinterpret_cast<const float4*>(srow + c);
+                        const float4 cc = *reinterpret_cast<const float4*>(csf + c);
+                        bad |= !isfinite(sv.x) || !isfinite(sv.y) || !isfinite(sv.z) || !isfinite(sv.w);
+                        v = make_float4(sv.x * cr * cc.x, sv.y * cr * cc.y, sv.z * cr * cc.z,
+                                        sv.w * cr * cc.w);
+                        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            if (c + t == r) {
+                                diag[r] = e[t];
+                            } else {
+                                mx = fmaxf(mx, fabsf(e[t]));
+                                if (heat && fabsf(e[t]) > heat_lam) ++*heat;
+                            }
+                        }
+                    }
+                    *reinterpret_cast<float4*>(out + c) = v;
+                    if (grow) *reinterpret_cast<float4*>(grow + c) = v;
+                    if (brow) *reinterpret_cast<float4*>(brow + c) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                o4[q] = v;
-                if (g4) g4[q] = v;
-                if (b4) b4[q] = z;
+                if (cmax) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+                    if (lane == 0) cmax[(size_t)r * nch + ch] = mx;
+                }
+                continue;
             }
-            return bad;
         }
-    }
-    for (int c = tid; c < ldp; c += nthr) {
-        T v = T(0);
-        if (c < p) {
-            const T s = srow[c];
-            bad |= !isfinite(s);
-            const T cc = sizeof(T) == 4 ? (T)csf[c] : (T)cs[c];
-            v = s * cr * cc;
-            if (c == r) diag[r] = v;
-            else if (heat && fabs(v) > heat_lam) ++*heat;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int c = c0 + lane + 32 * t;
+            if (c >= ldp) break;
+            T v = T(0);
+            if (c < p) {
+                const T sv = srow[c];
+                bad |= !isfinite(sv);
+                const T cc = sizeof(T) == 4 ? (T)csf[c] : (T)cs[c];
+                v = sv * cr * cc;
+                if (c == r) {
+                    diag[r] = v;
+                } else {
+                    mx = fmaxf(mx, (float)fabs(v));
+                    if (heat && fabs(v) > heat_lam) ++*heat;
+                }
+            }
+            out[c] = v;
+            if (grow) grow[c] = v;
+            if (brow) brow[c] = T(0);
         }
-        out[c] = v;
-        if (GT) GT[(size_t)r * ldp + c] = v;
-        if (BT) BT[(size_t)r * ldp + c] = T(0);
+        if (cmax) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+            if (lane == 0) cmax[(size_t)r * nch + ch] = mx;
+        }
     }
     return bad;
 }
@@ -445,6 +494,7 @@ struct ColCounters {
     unsigned long long sweeps = 0, moves = 0;        // full sweeps and their moves
     unsigned long long act_sweeps = 0, act_moves = 0;   // active-set phase
     int outer_max = 0, n_nc = 0, n_deg = 0, max_sw = 0;
+    int blk = 0;                                      // columns solved by the block solver
 };
 
 __device__ __forceinline__ void flush_counters(FitCtrl* ctrl, ColCounters& c) {
@@ -885,20 +935,23 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
 }
 
 // sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the sorted support (Eq. (14)).
+// Every product is formed in FP64 (for FP32 data the product of two FP32
+// values is exact in FP64) and every sum is carried in FP64.  Rows u of the
+// support run in turn and the lanes take the columns v, so no lane divides an
+// index; the row sums b_u (sum_v b_v S_uv) keep the FP64 work at one fused
+// multiply-add per pair.
 template <typename T>
 __device__ double residual_quadratic_form_list(int j, const Support<T>& s, const CDArgs<T>& a) {
-    // Every product b_v S_uv is formed in the data precision (one rounding)
-    // and every sum is carried in FP64; FP64 arithmetic is very slow on this
-    // part, so the per-pair FP64 work is one conversion and one add.
     const int lane = threadIdx.x & 31;
     const int n = s.n;
     double lin = 0.0, quad = 0.0;
     for (int u = lane; u < n; u += 32)
-        lin += (double)(s.val[u] * a.SC[(size_t)s.idx[u] * a.ldp + j]);
-    // pairs spread over the lanes: independent accumulators, short chains
-    for (int t = lane; t < n * n; t += 32) {
-        const int u = t / n, v = t - (t / n) * n;
-        quad += (double)(s.val[u] * s.val[v] * a.SC[(size_t)s.idx[u] * a.ldp + s.idx[v]]);
+        lin = fma((double)s.val[u], (double)a.SC[(size_t)s.idx[u] * a.ldp + j], lin);
+    for (int u = 0; u < n; ++u) {
+        const T* __restrict__ row = a.SC + (size_t)s.idx[u] * a.ldp;
+        double part = 0.0;
+        for (int v = lane; v < n; v += 32) part = fma((double)s.val[v], (double)row[s.idx[v]], part);
+        quad = fma((double)s.val[u], part, quad);
     }
     lin = warp_sum(lin);
     quad = warp_sum(quad);
@@ -920,6 +973,15 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
     T* saa = reinterpret_cast<T*>(cs.ci + num_chunks(a.ldp));
     double* prev = reinterpret_cast<double*>(saa + ACT_MAX * ACT_MAX);   // HS: (sigma, F(sigma))
     reset_chunks(cs, a.ldp);
+    if constexpr (STD) {
+        // b = 0: the gradient is row j of S^C, whose chunk maxima the
+        // standardisation pass wrote, so the first sweep may skip chunks too
+        if (a.chunk_max) {
+            const int nch = num_chunks(a.ldp);
+            const float* __restrict__ cm = a.chunk_max + (size_t)j * nch;
+            for (int c = lane; c < nch; c += 32) cs.ci[c] = ChunkInfo{cm[c], 0.f, 0u, 0};
+        }
+    }
     __syncwarp();
 
     double sigma = 1.0;                                  // sigma^(0) = 1, b = 0
@@ -940,6 +1002,7 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
             // by tol.  Otherwise a full sweep of every coordinate decides (the
             // stop rule of Algorithm 1).
             bool conv;
+            if (s.n > a.ovf_supp) return false;          // a heavy column: the block solver
             cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.act_moves, cs, conv);
             const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow, conv);
             ++cnt.sweeps;
@@ -993,6 +1056,410 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
     cnt.n_deg += (status & COL_DEGENERATE) != 0;
     __syncwarp();
     return true;
+}
+
+// ===========================================================================
+// Block solver for heavy columns.
+//
+// Algorithm 1 for one column by a whole block of BLK_THREADS threads, for the
+// columns whose support is too large for the lazy solver's active-set phase
+// (a hub's regression on its neighbours has 40-50 coefficients).  The block
+// keeps the whole gradient g_j = S_.j - S b_j and b_j in shared memory:
+//  - active-set phase: one warp runs cyclic sweeps over the support A (up to
+//    BLK_AMAX coordinates, two per lane, the block S_AA in shared memory)
+//    until a sweep moves nothing by tol; then the block forms g afresh from
+//    row j and the |A| support rows (no drift accumulates across phases);
+//  - sweep: the cyclic ascending pass of Algorithm 1 over all coordinates (or
+//    with the support held after a converged phase, as in the lazy solver).
+//    Every thread tests its coordinates, a block minimum finds the first
+//    coordinate whose update changes b, and the rank-1 update
+//    g -= S_.k delta (Proposition 2 on S) is applied by the whole block in
+//    the same pass that looks for the next mover, so one move costs one pass
+//    over g and one barrier;
+//  - sigma from Eq. (14) in FP64 over the support (FP64 products), and the
+//    safeguarded secant step of the per-column solvers.
+// ===========================================================================
+constexpr int BLK_THREADS = 256;
+constexpr int BLK_WARPS = BLK_THREADS / 32;
+constexpr int BLK_AMAX = 64;       // active-set phase: up to 64 coordinates, two per lane
+constexpr int BLK_LIST = 1024;     // sorted support list (sigma step, phase, g refresh)
+
+// Shared memory of the block solver: g and b (ldp each), S_AA, the support
+// list and the double-buffered candidate moves of the sweep.
+template <typename T>
+__host__ __device__ constexpr size_t block_smem_bytes(int ldp) {
+    return 2 * (size_t)ldp * sizeof(T) + (size_t)BLK_AMAX * BLK_AMAX * sizeof(T) +
+           (size_t)BLK_LIST * sizeof(int) + 2 * 2 * (size_t)BLK_THREADS * sizeof(T);
+}
+
+// Per-block scratch of the block solver (static shared memory).
+struct BlockScratch {
+    int red[2][BLK_WARPS];       // block minimum / counts, double-buffered by parity
+    double dred[BLK_WARPS];      // FP64 block sums
+    int nlist;
+    int col;
+};
+
+// Smallest v over the block (one barrier; `par` alternates the buffer so the
+// next call cannot overwrite values still being read).
+__device__ __forceinline__ int block_min_int(int v, BlockScratch& sc, int& par) {
+    v = __reduce_min_sync(FULL_MASK, v);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sc.red[par][warp] = v;
+    __syncthreads();
+    int m = sc.red[par][0];
+#pragma unroll
+    for (int w = 1; w < BLK_WARPS; ++w) m = min(m, sc.red[par][w]);
+    par ^= 1;
+    return m;
+}
+
+// Sum of v over the block in a fixed order (deterministic for a fixed block size).
+__device__ __forceinline__ double block_sum_d(double v, BlockScratch& sc) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sc.dred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < BLK_WARPS; ++w) t += sc.dred[w];
+    __syncthreads();
+    return t;
+}
+
+// Sorted support of b (ascending) into list[0, min(n, BLK_LIST)); returns n.
+template <typename T>
+__device__ int block_support_list(const T* __restrict__ b, int p, int* __restrict__ list,
+                                  BlockScratch& sc, int& par) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int total = 0;
+    for (int base = 0; base < p; base += BLK_THREADS) {
+        const int k = base + threadIdx.x;
+        const bool nz = k < p && b[k] != T(0);
+        const unsigned bal = __ballot_sync(FULL_MASK, nz);
+        if (lane == 0) sc.red[par][warp] = __popc(bal);
+        __syncthreads();
+        int off = total, tot = 0;
+#pragma unroll
+        for (int w = 0; w < BLK_WARPS; ++w) {
+            const int c = sc.red[par][w];
+            if (w < warp) off += c;
+            tot += c;
+        }
+        par ^= 1;
+        const int pos = off + __popc(bal & ((1u << lane) - 1u));
+        if (nz && pos < BLK_LIST) list[pos] = k;
+        total += tot;
+    }
+    __syncthreads();
+    return total;
+}
+
+// g = S_.j - sum_{l in A} S_.l b_l over the whole row (block-wide), A = list[0, n).
+template <typename T>
+__device__ void block_form_gradient(int j, T* __restrict__ g, const T* __restrict__ b,
+                                    const int* __restrict__ list, int n, const CDArgs<T>& a) {
+    const int ldp = a.ldp;
+    const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
+    for (int q = threadIdx.x; 4 * q < ldp; q += BLK_THREADS) {
+        const int k0 = 4 * q;
+        T acc[4];
+        load4g<T>(Sj + k0, acc);
+#pragma unroll 4
+        for (int e = 0; e < n; ++e) {
+            const int l = list[e];
+            const T v = b[l];
+            T r[4];
+            load4g<T>(a.SC + (size_t)l * ldp + k0, r);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc[t] = fma(-v, r[t], acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) g[k0 + t] = acc[t];
+    }
+}
+
+// Active-set phase of the block solver, run by warp 0 on A = list[0, n),
+// n <= BLK_AMAX: lane m holds coordinates A_m and A_{m+32}.  Reads and writes
+// b for the coordinates of A; g is formed afresh by the caller afterwards.
+// Returns the sweeps done; conv tells whether the last one moved nothing by tol.
+template <typename T, bool STD>
+__device__ int block_active_phase(int j, T* __restrict__ b, const int* __restrict__ list, int n,
+                                  const CDArgs<T>& a, T lam, T* __restrict__ saa,
+                                  unsigned long long& moves, bool& conv) {
+    const int lane = threadIdx.x & 31;
+    const int ldp = a.ldp;
+    for (int k = 0; k < n; ++k) {
+        const T* __restrict__ row = a.SC + (size_t)list[k] * ldp;
+        for (int m = lane; m < n; m += 32) saa[k * BLK_AMAX + m] = row[list[m]];
+    }
+    const int m0 = lane, m1 = lane + 32;
+    const bool h0 = m0 < n, h1 = m1 < n;
+    T b0 = h0 ? b[list[m0]] : T(0), b1 = h1 ? b[list[m1]] : T(0);
+    T g0 = h0 ? a.SC[(size_t)j * ldp + list[m0]] : T(0);
+    T g1 = h1 ? a.SC[(size_t)j * ldp + list[m1]] : T(0);
+    T s0 = T(1), s1 = T(1);
+    if constexpr (!STD) {
+        if (h0) s0 = a.diag[list[m0]];
+        if (h1) s1 = a.diag[list[m1]];
+    }
+    __syncwarp();
+    for (int l = 0; l < n; ++l) {
+        const T bl = __shfl_sync(FULL_MASK, l < 32 ? b0 : b1, l & 31);
+        if (h0) g0 = fma(-saa[l * BLK_AMAX + m0], bl, g0);
+        if (h1) g1 = fma(-saa[l * BLK_AMAX + m1], bl, g1);
+    }
+    conv = false;
+    int sw = 0;
+    while (sw < a.maxit) {
+        ++sw;
+        T md = T(0);
+        for (int k = 0; k < n; ++k) {
+            const int owner = k & 31;
+            const bool hi = k >= 32;
+            T d = T(0), nb = T(0);
+            if (lane == owner) {
+                const T gk = hi ? g1 : g0, bk = hi ? b1 : b0;
+                if constexpr (STD) nb = soft<T>(gk + bk, lam);                  // S_kk = 1
+                else {
+                    const T sk = hi ? s1 : s0;
+                    nb = soft<T>(gk + sk * bk, lam) / sk;
+                }
+                d = nb - bk;
+            }
+            d = __shfl_sync(FULL_MASK, d, owner);
+            if (d != T(0)) {
+                if (h0) g0 = fma(-saa[k * BLK_AMAX + m0], d, g0);
+                if (h1) g1 = fma(-saa[k * BLK_AMAX + m1], d, g1);
+                if (lane == owner) {
+                    if (hi) b1 = nb;
+                    else b0 = nb;
+                }
+                md = fmax(md, fabs(d));
+                ++moves;
+            }
+        }
+        if ((double)md < a.tol) {
+            conv = true;
+            break;
+        }
+    }
+    if (h0) b[list[m0]] = b0;
+    if (h1) b[list[m1]] = b1;
+    return sw;
+}
+
+// One sweep of the block solver (cyclic ascending, k != j; with `frozen` the
+// coordinates of the support keep their values).  Returns max |delta b|.
+// cand holds the candidate moves (new b, delta) of every thread, two buffers.
+template <typename T, bool STD>
+__device__ T block_sweep(int j, T* __restrict__ g, T* __restrict__ b, const CDArgs<T>& a, T lam,
+                         bool frozen, T* __restrict__ cand, unsigned long long& moves,
+                         BlockScratch& sc, int& par) {
+    const int tid = threadIdx.x;
+    const int p = a.p, ldp = a.ldp;
+    T maxd = T(0);
+    int ks = -1;                      // the move of the last pass, applied in this pass
+    T delta = T(0);
+    for (;;) {
+        const T* __restrict__ srow = a.SC + (size_t)(ks < 0 ? 0 : ks) * ldp;
+        T* __restrict__ cb = cand + (size_t)par * 2 * BLK_THREADS;
+        int kmin = INT_MAX;
+        for (int q = tid; 4 * q < ldp; q += BLK_THREADS) {
+            const int k0 = 4 * q;
+            T gv[4];
+            load4<T>(g + k0, gv);
+            if (ks >= 0) {            // rank-1 update g -= S_.ks delta (Proposition 2)
+                T r[4];
+                load4g<T>(srow + k0, r);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) gv[t] = fma(-delta, r[t], gv[t]);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) g[k0 + t] = gv[t];
+            }
+            if (kmin == INT_MAX && k0 + 3 > ks && k0 < p) {
+                T bv[4];
+                load4<T>(b + k0, bv);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int k = k0 + t;
+                    if (kmin == INT_MAX && k > ks && k < p && k != j && !(frozen && bv[t] != T(0))) {
+                        T nb;
+                        if constexpr (STD) {
+                            nb = soft<T>(gv[t] + bv[t], lam);                 // S_kk = 1
+                        } else {
+                            const T skk = a.diag[k];
+                            nb = soft<T>(gv[t] + skk * bv[t], lam) / skk;     // Soft(c, lambda)/S_kk
+                        }
+                        if (nb != bv[t]) {
+                            kmin = k;
+                            cb[tid] = nb;
+                            cb[BLK_THREADS + tid] = nb - bv[t];
+                        }
+                    }
+                }
+            }
+        }
+        const int kb = block_min_int(kmin, sc, par);    // barrier: g updated, candidates visible
+        if (kb == INT_MAX) break;
+        const int owner = (kb >> 2) % BLK_THREADS;      // the thread whose quads hold kb
+        delta = cb[BLK_THREADS + owner];
+        if (tid == owner) b[kb] = cb[owner];
+        maxd = fmax(maxd, fabs(delta));
+        ++moves;
+        ks = kb;
+    }
+    return maxd;
+}
+
+// sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the support list (block-wide),
+// FP64 products; a support longer than the list takes the rows from b itself.
+template <typename T>
+__device__ double block_quadratic_form(int j, const T* __restrict__ b, const int* __restrict__ list,
+                                       int n, const CDArgs<T>& a, BlockScratch& sc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ldp = a.ldp, p = a.p;
+    double lin = 0.0, quad = 0.0;
+    if (n <= BLK_LIST) {
+        for (int u = warp; u < n; u += BLK_WARPS) {
+            const int ku = list[u];
+            const T* __restrict__ row = a.SC + (size_t)ku * ldp;
+            double part = 0.0;
+            for (int v = lane; v < n; v += 32) {
+                const int kv = list[v];
+                part = fma((double)b[kv], (double)row[kv], part);
+            }
+            quad = fma((double)b[ku], part, quad);
+            if (lane == 0) lin = fma((double)b[ku], (double)row[j], lin);
+        }
+    } else {
+        for (int u = warp; u < p; u += BLK_WARPS) {
+            const T bu = b[u];
+            if (bu == T(0)) continue;
+            const T* __restrict__ row = a.SC + (size_t)u * ldp;
+            double part = 0.0;
+            for (int v = lane; v < p; v += 32)
+                if (b[v] != T(0)) part = fma((double)b[v], (double)row[v], part);
+            quad = fma((double)bu, part, quad);
+            if (lane == 0) lin = fma((double)bu, (double)row[j], lin);
+        }
+    }
+    lin = block_sum_d(lin, sc);
+    quad = block_sum_d(quad, sc);
+    return (double)a.SC[(size_t)j * ldp + j] - 2.0 * lin + quad;
+}
+
+// Algorithm 1 for column j by the whole block (see above).  Writes b_j (the
+// whole row j of BT), sigma_j and the column status.  Counters are kept
+// identically by every thread; the caller flushes thread 0's.
+template <typename T, bool STD>
+__device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& a,
+                                   ColCounters& cnt, BlockScratch& sc) {
+    const int tid = threadIdx.x;
+    const int ldp = a.ldp;
+    T* g = reinterpret_cast<T*>(smem);
+    T* b = g + ldp;
+    T* saa = b + ldp;
+    int* list = reinterpret_cast<int*>(saa + BLK_AMAX * BLK_AMAX);
+    T* cand = reinterpret_cast<T*>(list + BLK_LIST);
+    int par = 0;
+    {
+        const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
+        for (int k = tid; k < ldp; k += BLK_THREADS) {
+            g[k] = Sj[k];                                 // g = S_.j  (b = 0)
+            b[k] = T(0);
+        }
+    }
+    __syncthreads();
+    double sigma = 1.0;                                   // sigma^(0) = 1
+    double s_prev = 0.0, f_prev = 0.0;                    // last (sigma, F(sigma))
+    const unsigned long long sweeps0 = cnt.sweeps;
+    const double floor2 = 1e-12 * (double)a.SC[(size_t)j * ldp + j];
+    int status = COL_OK;
+    int r;
+    for (r = 0; r < a.maxit; ++r) {
+        const T lam = (T)(sigma * a.lambda0);
+        bool inner_ok = false;
+        for (int m = 0; m < a.maxit; ++m) {
+            // converge on the support first (when it fits the phase), then a
+            // sweep with the support held decides; otherwise a full sweep
+            // decides (Algorithm 1's stop), as in the lazy solver
+            const int n = block_support_list<T>(b, a.p, list, sc, par);
+            bool conv = n == 0;
+            if (n > 0 && n <= BLK_AMAX) {
+                int sw = 0;
+                bool c = false;
+                if (tid < 32) sw = block_active_phase<T, STD>(j, b, list, n, a, lam, saa,
+                                                              cnt.act_moves, c);
+                if (tid == 0) {
+                    sc.red[par][0] = sw;
+                    sc.red[par][1] = c ? 1 : 0;
+                }
+                __syncthreads();
+                sw = sc.red[par][0];
+                conv = sc.red[par][1] != 0;
+                par ^= 1;
+                cnt.act_sweeps += sw;
+                block_form_gradient<T>(j, g, b, list, n, a);
+                __syncthreads();
+            }
+            const T md = block_sweep<T, STD>(j, g, b, a, lam, conv, cand, cnt.moves, sc, par);
+            ++cnt.sweeps;
+            if ((double)md < a.tol) {
+                inner_ok = true;
+                break;
+            }
+        }
+        if (!inner_ok) status |= COL_NOT_CONVERGED;
+        const int n = block_support_list<T>(b, a.p, list, sc, par);
+        double q = block_quadratic_form<T>(j, b, list, n, a, sc);
+        if (q <= floor2) {
+            q = floor2;
+            status |= COL_DEGENERATE;
+        }
+        const double sn = sqrt(q);
+        if (fabs(sn - sigma) < a.tol) {
+            sigma = sn;
+            break;
+        }
+        double nxt = sn;
+        if (r > 0 && r + 1 < a.maxit && !(status & COL_DEGENERATE))
+            nxt = sigma_step(s_prev, f_prev, sigma, sn);
+        s_prev = sigma;
+        f_prev = sn;
+        sigma = nxt;
+    }
+    if (r == a.maxit) {
+        r = a.maxit - 1;
+        status |= COL_NOT_CONVERGED;
+    }
+    // b_j into row j of BT (the whole row, zeros included)
+    T* brow = a.BT + (size_t)j * ldp;
+    for (int k = tid; k < ldp; k += BLK_THREADS) brow[k] = b[k];
+    if (tid == 0) {
+        a.sigma[j] = sigma;
+        a.col_status[j] = status;
+    }
+    cnt.outer_max = max(cnt.outer_max, r + 1);
+    cnt.max_sw = max(cnt.max_sw, (int)(cnt.sweeps - sweeps0));
+    cnt.n_nc += (status & COL_NOT_CONVERGED) != 0;
+    cnt.n_deg += (status & COL_DEGENERATE) != 0;
+    ++cnt.blk;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void flush_counters_block(FitCtrl* ctrl, ColCounters& c) {
+    if (threadIdx.x == 0) {
+        if (c.blk) atomicAdd(&ctrl->block_cols, c.blk);
+        if (c.sweeps) atomicAdd(&ctrl->total_sweeps, c.sweeps);
+        if (c.moves) atomicAdd(&ctrl->moves, c.moves);
+        if (c.act_sweeps) atomicAdd(&ctrl->act_sweeps, c.act_sweeps);
+        if (c.act_moves) atomicAdd(&ctrl->act_moves, c.act_moves);
+        atomicMax(&ctrl->outer_max, c.outer_max);
+        atomicMax(&ctrl->max_col_sweeps, c.max_sw);
+        if (c.n_nc) atomicAdd(&ctrl->n_not_converged, c.n_nc);
+        if (c.n_deg) atomicAdd(&ctrl->n_degenerate, c.n_deg);
+    }
+    c = ColCounters();
 }
 
 // Theta (Eq. (4), Eq. (9), Proposition 1) over pairs of TS x TS tiles: the

@@ -39,9 +39,12 @@ struct FitCtrl {
     unsigned long long nnz;            // nonzero b at exit
     int inner_cap_hit;                 // joint rule: inner cap reached in some outer iteration
     int max_col_sweeps;                // largest per-column sweep count
-    int ovf_count;                     // columns handed from the lazy to the eager solver
-    int ovf_next;                      // eager solver's position in that queue
-    int pad[4];
+    int ovf_count;                     // columns handed from the lazy to the block (eager) solver
+    int ovf_next;                      // that solver's position in the queue
+    int n_heavy;                       // heavy columns: the first n_heavy of the heat order
+    int heavy_next;                    // block solver's position among them
+    int block_cols;                    // columns solved by the block solver
+    int pad[1];
     unsigned long long act_sweeps;     // lazy solver: sweeps over the support only
     unsigned long long act_moves;      // moves in those sweeps
 };
@@ -59,8 +62,12 @@ inline int padded_ld(int p) { return (p + 31) / 32 * 32; }
 // Byte offsets of the fit workspace (see spmesl_fit_workspace_bytes).
 struct FitLayout {
     int ldp;
-    size_t ctrl, cs, csf, sigma, col_status, active, active_next, flag, diag, SC, BT, GT, total;
+    size_t ctrl, cs, csf, sigma, col_status, active, active_next, flag, diag, cmax, SC, BT, GT,
+        total;
 };
+
+// 128-coordinate chunks of a padded row (the lazy solver's scan unit).
+inline int row_chunks(int ldp) { return (ldp + 127) / 128; }
 
 inline FitLayout fit_layout(int p, int precision) {
     FitLayout L{};
@@ -77,6 +84,7 @@ inline FitLayout fit_layout(int p, int precision) {
     L.active_next = off; off += align_up((size_t)p * 4, 256);
     L.flag = off;        off += align_up((size_t)p * 4, 256);
     L.diag = off;        off += align_up((size_t)p * s, 256);
+    L.cmax = off;        off += align_up((size_t)p * row_chunks(L.ldp) * 4, 256);
     L.SC = off;          off += mat;
     L.BT = off;          off += mat;
     L.GT = off;          off += mat;

@@ -8,8 +8,12 @@
 // change the process's device-memory footprint.  For them the fit's scratch
 // (standardised S, coefficients, gradients, control block) lives in one
 // file-scope __device__ array of kScratchBytes (64 MiB).  The array belongs
-// to the module: every GPU that loads this library holds it until the
-// process exits, whether the entry point is called or not.
+// to this library's module: the CUDA runtime loads the module (and commits
+// the 64 MiB on the device) when the first call on that device looks up the
+// array's address, and the device then holds it until the process exits.
+// So that first call changes the device-memory footprint; make it at
+// start-up, before memory is tight.  If the device cannot hold the array the
+// call returns SPMESL_ENOMEM.
 //
 // Host code cannot pass the array's name to a kernel (on the host it is only
 // a stand-in symbol, not a device address), so the first call on each device
@@ -72,9 +76,14 @@ extern "C" spmesl_status spmesl_fit_noalloc(const void* S, int n, int p, double 
     o.record_phase_times = 0;           // timing events are not created here
     void* scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
+    if (e == cudaErrorMemoryAllocation) return SPMESL_ENOMEM;   // no room for the array
     if (e != cudaSuccess) return SPMESL_ECUDA;
     spmesl_status s = spmesl_fit(S, n, p, lambda0, tol, maxit, &o, Theta, sigma, nullptr, scratch,
                                  kScratchBytes, stream);
     if (s != SPMESL_OK || !stats) return s;
-    return spmesl_fit_result(scratch, p, o.precision, stats, stream);
+    s = spmesl_fit_result(scratch, p, o.precision, stats, stream);
+    // the penalty level the fit used (the rule's value unless it was given)
+    stats->lambda0 = o.lambda_rule == SPMESL_LAMBDA_GIVEN ? lambda0
+                                                          : spmesl_lambda(o.lambda_rule, n, p);
+    return s;
 }

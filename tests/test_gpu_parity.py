@@ -149,6 +149,29 @@ def test_nonfinite_input_reported():
     assert e.value.status == sp.SPMESL_ENONFINITE
 
 
+def test_nonfinite_input_leaves_theta_untouched():
+    """ENONFINITE promises Theta untouched: a sentinel in Theta survives a fit
+    of an S holding a NaN (workspace fit and the allocation-free fit)."""
+    p = 40
+    S = torch.eye(p, dtype=torch.float32, device=DEV)
+    S[3, 5] = S[5, 3] = float("nan")
+    opts = sp.spmesl_default_opts()
+    opts.precision = sp.FP32
+    nb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
+    keep, ws = sp._workspace(nb, DEV)
+    for noalloc in (False, True):
+        T = torch.full((p, p), 7.25, dtype=torch.float64, device=DEV)
+        sg = torch.full((p,), -3.5, dtype=torch.float64, device=DEV)
+        st = sp.Stats()
+        if noalloc:
+            rc = sp.spmesl_fit_noalloc(S, 0, p, 0.1, 1e-6, 100, opts, T, sg, st)
+        else:
+            rc = sp.spmesl_fit(S, 0, p, 0.1, 1e-6, 100, opts, T, sg, st, ws, nb)
+        assert rc == sp.SPMESL_ENONFINITE
+        assert bool((T == 7.25).all()) and bool((sg == -3.5).all())
+    del keep
+
+
 def test_iteration_cap_reports_not_converged():
     prob = synth.make_problem("er", 64, 30, 2, dtype=np.float64)
     S = torch.from_numpy(oracle.gram(prob.X)).to(DEV)
@@ -188,9 +211,12 @@ def test_er_p2000_n200_fp32_full():
 
 
 # ---------------------------------------------------------------------------- gradient modes
-@pytest.mark.parametrize("gradient", [sp.GRADIENT_EAGER, sp.GRADIENT_LAZY])
+@pytest.mark.parametrize("gradient", [sp.GRADIENT_AUTO, sp.GRADIENT_EAGER, sp.GRADIENT_LAZY])
 @pytest.mark.parametrize("prec,standardize", [("fp32", True), ("fp64", True), ("fp32", False)])
 def test_gradient_modes_match_oracle(gradient, prec, standardize):
+    """The hub network's hub columns have supports of about 50: with AUTO they
+    run on the block solver (routed by heat when standardised, handed over by
+    the lazy solver otherwise), with LAZY on the lazy solver alone."""
     dt = np.float64 if prec == "fp64" else np.float32
     tol = 1e-9 if prec == "fp64" else 1e-6
     prob = synth.make_problem("hub_scaled", 300, 140, 17, dtype=dt)
@@ -199,14 +225,36 @@ def test_gradient_modes_match_oracle(gradient, prec, standardize):
     T, sg, st = sp.fit(S, prob.lambda0, tol=tol, maxit=2000, precision=prec, gradient=gradient,
                        standardize=standardize)
     assert st["status"] == sp.SPMESL_OK
+    if gradient == sp.GRADIENT_AUTO and standardize:
+        assert st["block_columns"] >= 10          # heat above 32: the hubs
+    elif gradient != sp.GRADIENT_AUTO:
+        assert st["block_columns"] == 0
     _, ref = _oracle_fit(prob.X, prob.lambda0, tol, 2000, standardize=standardize)
     _assert_parity(T.cpu().numpy(), ref)
 
 
-def test_lazy_support_overflow_falls_back_to_eager():
+@pytest.mark.parametrize("n,p,seed", [(90, 257, 3), (200, 1000, 8)])
+def test_block_solver_batch_equals_single_fits(n, p, seed):
+    """Heavy columns run on the block solver in a batch exactly as in a single
+    fit: every Theta of a mixed batch of hub networks equals its single fit."""
+    probs = [synth.make_problem("hub_scaled", p - 7 * i, n + 5 * i, seed + i, dtype=np.float32)
+             for i in range(3)]
+    inputs = [(torch.from_numpy(pr.X).to(DEV), pr.lambda0) for pr in probs]
+    bt = sp.Batch(inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000)
+    bt.run()
+    statuses, st = bt.result()
+    assert all(s == sp.SPMESL_OK for s in statuses) and st["block_columns"] > 0
+    for i, pr in enumerate(probs):
+        _, T, sg, _, _ = _gpu_fit(pr.X, pr.lambda0, 1e-6, 1000, "fp32")
+        assert np.array_equal(bt.Theta[i].cpu().numpy(), T)
+        assert np.array_equal(bt.sigma[i].cpu().numpy(), sg)
+    bt.close()
+
+
+def test_lazy_support_overflow_falls_back():
     """A tiny penalty with n >> p makes supports of ~p-1 > 512 entries: those
-    columns leave the lazy solver's list and are solved again by the eager
-    solver; the fit must still match the oracle."""
+    columns leave the lazy solver and are solved again by the block solver
+    (AUTO), or by the eager solver; the fit must still match the oracle."""
     prob = synth.make_problem("ar1", 700, 2800, 21, dtype=np.float32)
     lam = 0.0005
     Xd = torch.from_numpy(prob.X).to(DEV)
@@ -214,7 +262,7 @@ def test_lazy_support_overflow_falls_back_to_eager():
     Ta, sa, sta, Ba = sp.fit(S, lam, tol=1e-6, maxit=5000, precision="fp32",
                              gradient=sp.GRADIENT_AUTO, return_B=True)
     # some column's support exceeds the lazy list, so the fallback really ran
-    assert int((Ba != 0).sum(dim=0).max()) > 512
+    assert int((Ba != 0).sum(dim=0).max()) > 512 and sta["block_columns"] > 0
     Te, se, ste = sp.fit(S, lam, tol=1e-6, maxit=5000, precision="fp32",
                          gradient=sp.GRADIENT_EAGER)
     assert sta["status"] == sp.SPMESL_OK and ste["status"] == sp.SPMESL_OK

@@ -111,6 +111,18 @@ def test_errors():
     with pytest.raises(sp.SpmeslError) as e:
         sp.fit_residual(bad, prob.lambda0)
     assert e.value.status == sp.SPMESL_ENONFINITE
+    # Theta and sigma are left as the caller gave them
+    n, p = bad.shape
+    T = torch.full((p, p), 7.25, dtype=torch.float64, device=DEV)
+    sg = torch.full((p,), -3.5, dtype=torch.float64, device=DEV)
+    nb = sp.spmesl_fit_residual_workspace_bytes(n, p, sp.FP32)
+    keep, ws = sp._workspace(nb, DEV)
+    opts = sp.spmesl_default_opts()
+    rc = sp.spmesl_fit_residual(bad, n, p, p, prob.lambda0, 1e-6, 100, opts, T, sg, sp.Stats(),
+                                ws, nb)
+    assert rc == sp.SPMESL_ENONFINITE
+    assert bool((T == 7.25).all()) and bool((sg == -3.5).all())
+    del keep
     const = X.clone()
     const[:, 5] = 2.5                                     # zero variance once centred
     with pytest.raises(sp.SpmeslError) as e:

@@ -251,12 +251,21 @@ def test_status_flags():
     _, S = _random_cov(30, 60, 6)
     out = oracle.spmesl(S, 0.1, tol=1e-12, maxit=1)
     assert out["worst"] == oracle.COL_NOT_CONVERGED
-    # n < p with a tiny penalty: a perfect fit drives sigma to the floor
+    # exactly collinear columns: the p = 2 closed form gives
+    # sigma^2 = (1 - rho^2) / (1 - lambda0^2) = 0 at rho = 1, so every column
+    # reaches the floor sigma^2 = 1e-12 S_jj and is flagged degenerate (and
+    # nothing else), with sigma at the floor
+    S2 = np.array([[1.0, 1.0], [1.0, 1.0]])
+    out2 = oracle.spmesl(S2, 0.01, tol=1e-9, maxit=200)
+    assert out2["worst"] == oracle.COL_DEGENERATE
+    assert np.all(out2["status"] == oracle.COL_DEGENERATE)
+    assert np.allclose(out2["sigma"], 1e-6, rtol=1e-12)
+    # a third column that is an exact combination of the other two (n = 5)
     rng = np.random.default_rng(0)
-    X = rng.standard_normal((4, 8))
-    S2 = X.T @ X / 4
-    out2 = oracle.spmesl(S2, 1e-7, tol=1e-9, maxit=200)
-    assert np.any(out2["status"] == oracle.COL_DEGENERATE) or out2["worst"] >= 1
+    x = rng.standard_normal((5, 2))
+    X = np.column_stack([x[:, 0], x[:, 1], x[:, 0] - 0.5 * x[:, 1]])
+    out3 = oracle.spmesl(X.T @ X / 5, 0.01, tol=1e-9, maxit=200)
+    assert np.all(out3["status"] == oracle.COL_DEGENERATE)
 
 
 # ---------------------------------------------------------------- penalty levels
