@@ -79,12 +79,16 @@ typedef enum {
  * sweeps each column's support alone before every certifying sweep, so its
  * iterates take another path to the same solution. */
 typedef enum {
-    SPMESL_GRADIENT_AUTO = 0,   /* lazy, with the eager solver for columns whose support
-                                   outgrows the lazy solver's list (256 entries) */
+    SPMESL_GRADIENT_AUTO = 0,   /* lazy, and the block solver for heavy columns: those whose
+                                   heat exceeds opts.heavy_heat in fits of at least
+                                   opts.heavy_min_p columns (from the start, beside the lazy
+                                   launch) and those whose support outgrows the lazy solver's
+                                   32-coordinate active-set phase (after it) */
     SPMESL_GRADIENT_EAGER = 1,  /* g_j and b_j stored in shared memory, rank-1 update of the
                                    whole g_j after every coordinate move */
     SPMESL_GRADIENT_LAZY = 2    /* only the support of b_j stored; each 128-coordinate slice of
-                                   g_j formed from S rows when the sweep reaches it (same as AUTO) */
+                                   g_j formed from S rows when the sweep reaches it; the block
+                                   solver only for supports beyond the lazy list (256) */
 } spmesl_gradient;
 
 typedef struct {
@@ -104,7 +108,13 @@ typedef struct {
     int32_t diagnostics;        /* 1: after the fit, one more launch checks every column's
                                    (b_j, sigma_j) in FP64 on the device and fills kkt_viol,
                                    dual_gap and err_est of spmesl_stats (0: not computed) */
-    int32_t reserved[6];
+    int32_t heavy_heat;         /* SPMESL_GRADIENT_AUTO on a standardised fit: a column whose
+                                   heat (off-diagonal |S^C_jk| above lambda0) exceeds this goes to
+                                   the block solver from the start; 0 = 32, at most 62 */
+    int32_t heavy_min_p;        /* ... only in fits with p >= heavy_min_p (0 = 4096; < 0: never).
+                                   In any fit a column whose support outgrows the lazy solver's
+                                   32-coordinate active-set phase is handed over to it */
+    int32_t reserved[4];
 } spmesl_opts;
 
 typedef struct {
@@ -329,8 +339,9 @@ spmesl_status spmesl_fit_coefficients(const void* workspace, int p, int precisio
  *            beta, ms_total = whole call).
  *   workspace  spmesl_scaled_lasso_workspace_bytes(n, p, precision) bytes,
  *            256-byte aligned, owned by the caller.
- * opts: precision, standardize, center and lambda_rule are used; the inner
- * rule is the per-column one and the gradient the lazy one.
+ * opts: precision, standardize, center, lambda_rule, heavy_heat and
+ * heavy_min_p are used; the inner rule is the per-column one and the gradient
+ * SPMESL_GRADIENT_AUTO (the column solved as in a whole fit).
  * Errors: EINVAL (NULL pointers, n < 1, p < 1, p + 1 above spmesl_max_p,
  * tol <= 0, maxit < 1, short or misaligned workspace, no usable lambda0),
  * ENONFINITE (non-finite data), ECUDA.

@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("inner_rule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("record_phase_times", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("gradient", ctypes.c_int32), ("diagnostics", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("heavy_heat", ctypes.c_int32), ("heavy_min_p", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Problem(ctypes.Structure):
@@ -411,7 +412,8 @@ def fit_residual(X, lambda0, tol=1e-6, maxit=1000, precision="fp32", standardize
 
 def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=True,
         inner_rule=INNER_COLUMN, lambda_rule=LAMBDA_GIVEN, warps_per_block=0,
-        gradient=GRADIENT_AUTO, return_B=False, stream=None):
+        gradient=GRADIENT_AUTO, return_B=False, heavy_heat=0, heavy_min_p=0, diagnostics=False,
+        stream=None):
     """One fit on a CUDA covariance tensor.  Synchronises and returns
     (Theta, sigma, stats_dict[, B])."""
     import torch
@@ -425,6 +427,9 @@ def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=Tru
     opts.lambda_rule = int(lambda_rule)
     opts.warps_per_block = int(warps_per_block)
     opts.gradient = int(gradient)
+    opts.heavy_heat = int(heavy_heat)
+    opts.heavy_min_p = int(heavy_min_p)
+    opts.diagnostics = int(bool(diagnostics))
     Theta = torch.empty((p, p), dtype=torch.float64, device=S.device)
     sigma = torch.empty(p, dtype=torch.float64, device=S.device)
     nb = spmesl_fit_workspace_bytes(p, prec)
@@ -486,7 +491,8 @@ class Batch:
 
     def __init__(self, inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000,
                  use_graph=False, warps_per_block=0, center=False, record_phase_times=False,
-                 gradient=GRADIENT_AUTO, device=None):
+                 gradient=GRADIENT_AUTO, heavy_heat=0, heavy_min_p=0, diagnostics=False,
+                 device=None):
         import torch
         _require_cuda()
         prec = _prec(precision)
@@ -515,6 +521,9 @@ class Batch:
         opts.center = int(bool(center))
         opts.record_phase_times = int(bool(record_phase_times))
         opts.gradient = int(gradient)
+        opts.heavy_heat = int(heavy_heat)
+        opts.heavy_min_p = int(heavy_min_p)
+        opts.diagnostics = int(bool(diagnostics))
         rc, self.handle = spmesl_batch_create(arr, self.count, tol, maxit, opts)
         _check(rc, "spmesl_batch_create")
         self.ws_bytes = spmesl_batch_workspace_bytes(self.handle)

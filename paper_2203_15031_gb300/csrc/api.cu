@@ -236,6 +236,8 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
     f.inner_rule = o.inner_rule;
     f.warps_per_block = o.warps_per_block;
     f.gradient = o.gradient;
+    f.heavy_heat = o.heavy_heat;
+    f.heavy_min_p = o.heavy_min_p;
     f.Theta = Theta;
     f.sigma_out = sigma;
     f.ws = static_cast<unsigned char*>(workspace);
@@ -374,7 +376,9 @@ spmesl_status spmesl_scaled_lasso(const void* X, const void* y, int n, int p, do
         f.standardize = o.standardize ? 1 : 0;
         f.inner_rule = SPMESL_INNER_COLUMN;
         f.warps_per_block = 0;
-        f.gradient = SPMESL_GRADIENT_LAZY;
+        f.gradient = SPMESL_GRADIENT_AUTO;
+        f.heavy_heat = o.heavy_heat;
+        f.heavy_min_p = o.heavy_min_p;
         f.Theta = nullptr;
         f.sigma_out = sigma;
         f.ws = ws + L.fit;

@@ -49,7 +49,7 @@ struct BatchFit {
     int n, p, ldp;
     int col_start, gram_start, theta_start;
     int split_start;      // first block of the batched split/transpose launch
-    int pad;
+    int prep_start;       // first block of the standardisation launch
 };
 
 thread_local bool g_batch_pageable_staging = false;
@@ -124,27 +124,46 @@ __global__ void batch_prep_diag_kernel(const BatchFit* __restrict__ fits, int st
     }
 }
 
-// blockIdx.y = fit; blocks stride over the fit's rows (same arithmetic as
-// the single-fit prep_matrix_kernel; BT is cleared on the side stream).  With heat,
+// One block per PREP_ROWS rows of one fit (found from the block prefix, so
+// every block has the same work whatever the fit sizes); same arithmetic as
+// the single-fit prep_matrix_kernel; BT is cleared on the side stream.  With heat,
 // also counts per column the off-diagonal entries of the standardised matrix
 // above lambda0: the coordinates that can move in the column's first sweep,
-// a predictor of how long the column takes.
+// a predictor of how long the column takes.  In fits below heavy_min_p
+// columns the count is capped at heavy_heat, so none of their columns is
+// routed to the block solver by heat (the single-fit rule).
+constexpr int PREP_ROWS = 4;
 template <typename T>
-__global__ void batch_prep_matrix_kernel(const BatchFit* __restrict__ fits, int* __restrict__ heat) {
-    const BatchFit& f = fits[blockIdx.y];
+__global__ void __launch_bounds__(256) batch_prep_matrix_kernel(const BatchFit* __restrict__ fits,
+                                                                const int* __restrict__ prep_prefix,
+                                                                int count, int* __restrict__ heat,
+                                                                int heavy_heat, int heavy_min_p) {
+    __shared__ int wsum[8];
+    const int fi = find_fit(prep_prefix, count, blockIdx.x);
+    const BatchFit& f = fits[fi];
     bool bad = false;
-    for (int r = blockIdx.x; r < f.p; r += gridDim.x) {
+    const int r0 = (blockIdx.x - f.prep_start) * PREP_ROWS;
+    const int cap = f.p >= heavy_min_p ? INT_MAX : heavy_heat;
+    for (int r = r0; r < min(f.p, r0 + PREP_ROWS); ++r) {
         int cnt = 0;
         bad |= standardize_row<T>(static_cast<const T*>(f.S), f.p, f.ldp, r, f.cs, f.csf,
                                   static_cast<T*>(f.SC), nullptr, nullptr,
                                   static_cast<T*>(f.diag), threadIdx.x, blockDim.x,
                                   (T)f.lambda0, heat ? &cnt : nullptr, f.cmax);
-        if (cnt) atomicAdd(&heat[f.col_start + r], cnt);
+        if (heat) {
+            cnt = __reduce_add_sync(FULL_MASK, cnt);
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int t = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+                heat[f.col_start + r] = min(t, cap);
+            }
+            __syncthreads();
+        }
     }
     if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
 }
-
-
 
 template <typename T>
 __device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, int maxit,
@@ -254,7 +273,7 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
 // (from_overflow = 0, beside the lazy launch) or over the columns the lazy
 // launch handed over (from_overflow = 1, after it); one block per column.
 template <typename T, bool STD>
-__global__ void __launch_bounds__(BLK_THREADS) batch_cd_block_kernel(const BatchFit* __restrict__ fits,
+__global__ void __launch_bounds__(BLK_THREADS, 1) batch_cd_block_kernel(const BatchFit* __restrict__ fits,
                                                                      const int* __restrict__ col_prefix,
                                                                      int count, double tol, int maxit,
                                                                      BatchHeader* hdr,
@@ -337,7 +356,7 @@ struct FitPlan {
     size_t off_ctrl, off_cs, off_csf, off_sigma, off_status, off_diag, off_cmax, off_mu, off_Sg, off_SC,
         off_BT;
     size_t off_XhT, off_XlT;
-    int col_start, gram_start, theta_start, split_start;
+    int col_start, gram_start, theta_start, split_start, prep_start;
 };
 
 int num_sms() {
@@ -376,10 +395,13 @@ struct spmesl_batch {
     int maxit = 1000;
     int warps_per_block = 0;       // 0 = automatic
     int gradient = SPMESL_GRADIENT_AUTO;
+    int heavy_heat = 0, heavy_min_p = 0;   // routing limits of spmesl_opts (0: defaults)
     size_t off_ovf = 0;            // queue of columns for the eager launch (total_cols ints)
     size_t off_heat = 0, off_order = 0;   // per-column heat and the lazy queue's order
     std::vector<FitPlan> plan;     // ordered by decreasing p
     size_t off_hdr = 0, off_desc = 0, off_colp = 0, off_gramp = 0, off_thetap = 0, off_ctrls = 0;
+    size_t off_prepp = 0;          // block prefix of the standardisation launch
+    int total_prep = 0;
     // SPMESL_MIXED: tensor-core Gram table, fit of every tile, split prefixes
     size_t off_tcfit = 0, off_tilefit = 0, off_splitp = 0;
     int total_split = 0;
@@ -449,8 +471,6 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     }
     batch_prep_diag_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits,
                                                                                    b->standardize);
-    // rows per fit spread over blocks; enough blocks overall to fill the GPU
-    const int mx = std::max(1, std::min(b->max_p, (num_sms() * 8 + count - 1) / count));
     // column order for the lazy launch (standardised working matrix only);
     // with AUTO the heavy columns lead it and go to the block solver
     const bool lazy_order = b->gradient != SPMESL_GRADIENT_EAGER && b->standardize;
@@ -458,13 +478,13 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     const bool heavy = route && lazy_order;
     int* heat = reinterpret_cast<int*>(ws + b->off_heat);
     int* order = reinterpret_cast<int*>(ws + b->off_order);
-    if (lazy_order &&
-        (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)b->total_cols, st)) != cudaSuccess)
-        return e;
-    batch_prep_matrix_kernel<T><<<dim3(mx, count), 256, 0, st>>>(fits, lazy_order ? heat : nullptr);
+    const int hheat = heavy_heat_of(b->heavy_heat);
+    batch_prep_matrix_kernel<T><<<b->total_prep, 256, 0, st>>>(
+        fits, reinterpret_cast<const int*>(ws + b->off_prepp), count, lazy_order ? heat : nullptr,
+        hheat, heavy_min_p_of(b->heavy_min_p));
     if (lazy_order)
         order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, b->total_cols, order,
-                                                 heavy ? &hdr->n_heavy : nullptr);
+                                                 heavy ? &hdr->n_heavy : nullptr, hheat);
 
     const size_t budget = (size_t)max_smem_block() - 1024;
     const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
@@ -562,6 +582,7 @@ bool stage_table(spmesl_batch* b, unsigned char* ws) {
     int* colp = reinterpret_cast<int*>(b->pinned + (b->off_colp - b->off_desc));
     int* gramp = reinterpret_cast<int*>(b->pinned + (b->off_gramp - b->off_desc));
     int* thetap = reinterpret_cast<int*>(b->pinned + (b->off_thetap - b->off_desc));
+    int* prepp = reinterpret_cast<int*>(b->pinned + (b->off_prepp - b->off_desc));
     for (int i = 0; i < b->count; ++i) {
         const FitPlan& f = b->plan[i];
         BatchFit d{};
@@ -591,6 +612,7 @@ bool stage_table(spmesl_batch* b, unsigned char* ws) {
         d.col_start = f.col_start;
         d.gram_start = f.gram_start;
         d.theta_start = f.theta_start;
+        d.prep_start = f.prep_start;
         d.split_start = f.split_start;
         t[i] = d;
         if (mixed) {
@@ -609,10 +631,12 @@ bool stage_table(spmesl_batch* b, unsigned char* ws) {
         colp[i] = f.col_start;
         gramp[i] = f.gram_start;
         thetap[i] = f.theta_start;
+        prepp[i] = f.prep_start;
     }
     colp[b->count] = b->total_cols;
     gramp[b->count] = b->total_gram;
     thetap[b->count] = b->total_theta;
+    prepp[b->count] = b->total_prep;
     if (mixed) splitp[b->count] = b->total_split;
     b->table_ws = ws;
     return true;
@@ -660,6 +684,8 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->record_phase_times = o.record_phase_times ? 1 : 0;
     b->warps_per_block = o.warps_per_block;
     b->gradient = o.gradient;
+    b->heavy_heat = o.heavy_heat;
+    b->heavy_min_p = o.heavy_min_p;
     b->tol = tol;
     b->maxit = maxit;
     std::vector<int> order(count);
@@ -680,6 +706,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->off_colp = off;  off += align_up(sizeof(int) * (count + 1), 256);
     b->off_gramp = off; off += align_up(sizeof(int) * (count + 1), 256);
     b->off_thetap = off; off += align_up(sizeof(int) * (count + 1), 256);
+    b->off_prepp = off; off += align_up(sizeof(int) * (count + 1), 256);
     if (mixed) {
         b->off_tcfit = off;   off += align_up(sizeof(TcFit) * count, 256);
         b->off_tilefit = off; off += align_up(sizeof(int) * (size_t)std::max<long long>(tc_tiles, 1), 256);
@@ -687,7 +714,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     }
     b->table_bytes = off - b->off_desc;
     b->off_ctrls = off; off += (size_t)256 * count;      // one FitCtrl slot per fit
-    int cols = 0, gram = 0, theta = 0, split = 0;
+    int cols = 0, gram = 0, theta = 0, split = 0, prep = 0;
     for (int k = 0; k < count; ++k) {
         const spmesl_problem& q = probs[order[k]];
         FitPlan f{};
@@ -732,6 +759,8 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
             gram += t * (t + 1) / 2;
         }
         f.theta_start = theta;
+        f.prep_start = prep;
+        prep += (f.p + PREP_ROWS - 1) / PREP_ROWS;
         theta += o.precision == SPMESL_FP64 ? theta_pairs<double>(f.p) : theta_pairs<float>(f.p);
         b->max_ldp = std::max(b->max_ldp, f.ldp);
         b->max_p = std::max(b->max_p, f.p);
@@ -742,6 +771,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->total_gram = gram;
     b->total_split = split;
     b->total_theta = theta;
+    b->total_prep = prep;
     b->off_ovf = off;
     off += align_up(sizeof(int) * (size_t)cols, 256);
     b->off_heat = off;

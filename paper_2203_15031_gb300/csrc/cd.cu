@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(512) cd_column_lazy_kernel(CDArgs<T> a) {
 // the lazy kernel) or the columns the lazy solver handed over (from_overflow
 // = 1, after it).
 template <typename T, bool STD>
-__global__ void __launch_bounds__(BLK_THREADS) cd_column_block_kernel(CDArgs<T> a,
+__global__ void __launch_bounds__(BLK_THREADS, 1) cd_column_block_kernel(CDArgs<T> a,
                                                                       int from_overflow) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockScratch sc;
@@ -480,8 +480,9 @@ static cudaError_t side_resources(SideRes** out) {
 }
 
 // ctrl->n_heavy = 1 when the one column of a single regression is heavy.
-__global__ void heavy_flag_kernel(const int* __restrict__ heat, int* __restrict__ n_heavy) {
-    if (threadIdx.x == 0) *n_heavy = heat[0] > HEAVY_HEAT ? 1 : 0;
+__global__ void heavy_flag_kernel(const int* __restrict__ heat, int* __restrict__ n_heavy,
+                                  int heavy_heat) {
+    if (threadIdx.x == 0) *n_heavy = heat[0] > heavy_heat ? 1 : 0;
 }
 
 // Persistent grid of the block solver for this size.
@@ -531,10 +532,12 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     const bool joint = !single && f.inner_rule == SPMESL_INNER_JOINT;
     // Lazy launch shape (warps per block, blocks per SM).
     const bool lazy = single || (!joint && f.gradient != SPMESL_GRADIENT_EAGER);
-    // AUTO: heavy columns (heat above HEAVY_HEAT) go to the block solver beside
-    // the lazy launch, and the lazy solver hands over a column whose support
-    // outgrows its active-set phase; LAZY: the lazy solver keeps every column
-    // its list can hold.
+    // AUTO: heavy columns (heat above heavy_heat, in fits of at least
+    // heavy_min_p columns) go to the block solver beside the lazy launch, and
+    // the lazy solver hands over a column whose support outgrows its
+    // active-set phase; LAZY: the lazy solver keeps every column its list can
+    // hold.  Heat overstates the support of small fits, whose slices are cheap
+    // anyway, so the routing by heat is kept to large fits.
     const bool route = lazy && f.gradient == SPMESL_GRADIENT_AUTO;
     a.ovf_supp = route ? ACT_MAX : LAZY_CAP;
     auto lk = cd_column_lazy_kernel<T, STD>;
@@ -556,7 +559,8 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     // when there are more columns than resident warps or when heavy columns
     // are routed.  The active index vectors are the joint rule's; the column
     // rule lends them to the heat counts and the order.
-    const bool heavy = route && f.standardize;
+    const int hheat = heavy_heat_of(f.heavy_heat);
+    const bool heavy = route && f.standardize && f.p >= heavy_min_p_of(f.heavy_min_p);
     const bool ordered = !single && lazy && f.standardize &&
                          (heavy || f.p > g_num_sms * lper_sm * LW);
     int* heat = (ordered || (single && heavy)) ? a.active_next : nullptr;
@@ -581,14 +585,15 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
             reinterpret_cast<T*>(ws + L.diag), joint ? 1 : 0, ctrl, (T)f.lambda0, heat, cmax);
     }
     if (ordered) {
-        order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, f.p, a.active, heavy ? &ctrl->n_heavy : nullptr);
+        order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, f.p, a.active, heavy ? &ctrl->n_heavy : nullptr,
+                                                 hheat);
         a.order = a.active;
     }
     if (single) {
         // a queue of one column: active[j] = j after prep_diag_kernel
         a.order = a.active + f.response_col;
         a.n_queue = 1;
-        if (heavy) heavy_flag_kernel<<<1, 32, 0, st>>>(heat + f.response_col, &ctrl->n_heavy);
+        if (heavy) heavy_flag_kernel<<<1, 32, 0, st>>>(heat + f.response_col, &ctrl->n_heavy, hheat);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 

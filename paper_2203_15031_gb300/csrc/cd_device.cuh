@@ -41,12 +41,13 @@ namespace {
 // counting sort, one block), so the longest column solves start first instead
 // of in the tail of the launch.  Ties in any order: a column's result does not
 // depend on when it runs.  With n_heavy, also the number of columns whose heat
-// exceeds HEAVY_HEAT: they lead the order and go to the block solver.
+// exceeds heavy_heat (< HEAT_BINS - 1): they lead the order and go to the
+// block solver.
 constexpr int HEAT_BINS = 64;
-constexpr int HEAVY_HEAT = 32;
 __global__ void __launch_bounds__(1024) order_by_heat_kernel(const int* __restrict__ heat, int n,
                                                           int* __restrict__ order,
-                                                          int* __restrict__ n_heavy) {
+                                                          int* __restrict__ n_heavy,
+                                                          int heavy_heat) {
     __shared__ int bin[HEAT_BINS];
     const int t = threadIdx.x;
     if (t < HEAT_BINS) bin[t] = 0;
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(1024) order_by_heat_kernel(const int* __restri
             const int c = bin[h];
             bin[h] = run;
             run += c;
-            if (h == HEAVY_HEAT + 1 && n_heavy) *n_heavy = run;
+            if (h == heavy_heat + 1 && n_heavy) *n_heavy = run;
         }
     }
     __syncthreads();
@@ -1079,17 +1080,19 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
 //  - sigma from Eq. (14) in FP64 over the support (FP64 products), and the
 //    safeguarded secant step of the per-column solvers.
 // ===========================================================================
-constexpr int BLK_THREADS = 256;
+constexpr int BLK_THREADS = 512;
 constexpr int BLK_WARPS = BLK_THREADS / 32;
 constexpr int BLK_AMAX = 64;       // active-set phase: up to 64 coordinates, two per lane
 constexpr int BLK_LIST = 1024;     // sorted support list (sigma step, phase, g refresh)
 
 // Shared memory of the block solver: g and b (ldp each), S_AA, the support
-// list and the double-buffered candidate moves of the sweep.
+// list, the double-buffered candidate moves of the sweep and the support S_AA
+// was gathered for.
 template <typename T>
 __host__ __device__ constexpr size_t block_smem_bytes(int ldp) {
     return 2 * (size_t)ldp * sizeof(T) + (size_t)BLK_AMAX * BLK_AMAX * sizeof(T) +
-           (size_t)BLK_LIST * sizeof(int) + 2 * 2 * (size_t)BLK_THREADS * sizeof(T);
+           (size_t)BLK_LIST * sizeof(int) + 2 * 2 * (size_t)BLK_THREADS * sizeof(T) +
+           (size_t)BLK_AMAX * sizeof(int);
 }
 
 // Per-block scratch of the block solver (static shared memory).
@@ -1127,54 +1130,97 @@ __device__ __forceinline__ double block_sum_d(double v, BlockScratch& sc) {
 }
 
 // Sorted support of b (ascending) into list[0, min(n, BLK_LIST)); returns n.
+// Each thread counts the nonzeros of its own contiguous segment of b, a block
+// scan gives the segment offsets, and each thread writes its entries.
 template <typename T>
 __device__ int block_support_list(const T* __restrict__ b, int p, int* __restrict__ list,
                                   BlockScratch& sc, int& par) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int total = 0;
-    for (int base = 0; base < p; base += BLK_THREADS) {
-        const int k = base + threadIdx.x;
-        const bool nz = k < p && b[k] != T(0);
-        const unsigned bal = __ballot_sync(FULL_MASK, nz);
-        if (lane == 0) sc.red[par][warp] = __popc(bal);
-        __syncthreads();
-        int off = total, tot = 0;
+    const int seg = (p + BLK_THREADS - 1) / BLK_THREADS;
+    const int k0 = min(p, (int)threadIdx.x * seg), k1 = min(p, k0 + seg);
+    int c = 0;
+    for (int k = k0; k < k1; ++k) c += b[k] != T(0);
+    int incl = c;
 #pragma unroll
-        for (int w = 0; w < BLK_WARPS; ++w) {
-            const int c = sc.red[par][w];
-            if (w < warp) off += c;
-            tot += c;
-        }
-        par ^= 1;
-        const int pos = off + __popc(bal & ((1u << lane) - 1u));
-        if (nz && pos < BLK_LIST) list[pos] = k;
-        total += tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += u;
     }
+    if (lane == 31) sc.red[par][warp] = incl;
+    __syncthreads();
+    int off = incl - c, total = 0;
+#pragma unroll
+    for (int w = 0; w < BLK_WARPS; ++w) {
+        const int t = sc.red[par][w];
+        if (w < warp) off += t;
+        total += t;
+    }
+    par ^= 1;
+    for (int k = k0; k < k1 && off < BLK_LIST; ++k)
+        if (b[k] != T(0)) list[off++] = k;
     __syncthreads();
     return total;
 }
 
 // g = S_.j - sum_{l in A} S_.l b_l over the whole row (block-wide), A = list[0, n).
+// A thread takes QG of its quads at once and reads R support rows for each, so
+// QG * R independent loads are in flight; the products are accumulated in
+// the order of the list.
 template <typename T>
 __device__ void block_form_gradient(int j, T* __restrict__ g, const T* __restrict__ b,
                                     const int* __restrict__ list, int n, const CDArgs<T>& a) {
+    constexpr int QG = sizeof(T) == 4 ? 2 : 1, R = 4;
     const int ldp = a.ldp;
     const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
-    for (int q = threadIdx.x; 4 * q < ldp; q += BLK_THREADS) {
-        const int k0 = 4 * q;
-        T acc[4];
-        load4g<T>(Sj + k0, acc);
-#pragma unroll 4
-        for (int e = 0; e < n; ++e) {
-            const int l = list[e];
-            const T v = b[l];
-            T r[4];
-            load4g<T>(a.SC + (size_t)l * ldp + k0, r);
+    for (int q0 = threadIdx.x; 4 * q0 < ldp; q0 += QG * BLK_THREADS) {
+        T acc[QG][4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) acc[t] = fma(-v, r[t], acc[t]);
+        for (int u = 0; u < QG; ++u) {
+            const int k0 = 4 * (q0 + u * BLK_THREADS);
+            if (k0 < ldp) load4g<T>(Sj + k0, acc[u]);
+        }
+        int e = 0;
+        for (; e + R <= n; e += R) {
+            T r[R][QG][4];
+#pragma unroll
+            for (int v = 0; v < R; ++v) {
+                const T* __restrict__ row = a.SC + (size_t)list[e + v] * ldp;
+#pragma unroll
+                for (int u = 0; u < QG; ++u) {
+                    const int k0 = 4 * (q0 + u * BLK_THREADS);
+                    if (k0 < ldp) load4g<T>(row + k0, r[v][u]);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < R; ++v) {
+                const T bv = b[list[e + v]];
+#pragma unroll
+                for (int u = 0; u < QG; ++u)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) acc[u][t] = fma(-bv, r[v][u][t], acc[u][t]);
+            }
+        }
+        for (; e < n; ++e) {
+            const T* __restrict__ row = a.SC + (size_t)list[e] * ldp;
+            const T bv = b[list[e]];
+#pragma unroll
+            for (int u = 0; u < QG; ++u) {
+                const int k0 = 4 * (q0 + u * BLK_THREADS);
+                if (k0 < ldp) {
+                    T r[4];
+                    load4g<T>(row + k0, r);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) acc[u][t] = fma(-bv, r[t], acc[u][t]);
+                }
+            }
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) g[k0 + t] = acc[t];
+        for (int u = 0; u < QG; ++u) {
+            const int k0 = 4 * (q0 + u * BLK_THREADS);
+            if (k0 < ldp)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) g[k0 + t] = acc[u][t];
+        }
     }
 }
 
@@ -1182,17 +1228,45 @@ __device__ void block_form_gradient(int j, T* __restrict__ g, const T* __restric
 // n <= BLK_AMAX: lane m holds coordinates A_m and A_{m+32}.  Reads and writes
 // b for the coordinates of A; g is formed afresh by the caller afterwards.
 // Returns the sweeps done; conv tells whether the last one moved nothing by tol.
+// One move is the critical path of the phase: every lane forms the candidate
+// of its slot, the owner's change is broadcast by one shuffle, and every lane
+// updates its two gradients with the column of S_AA loaded one move ahead.  A
+// zero change adds exact zeros, so no lane branches on it.
 template <typename T, bool STD>
 __device__ int block_active_phase(int j, T* __restrict__ b, const int* __restrict__ list, int n,
                                   const CDArgs<T>& a, T lam, T* __restrict__ saa,
+                                  int* __restrict__ saa_list, int& saa_n,
                                   unsigned long long& moves, bool& conv) {
     const int lane = threadIdx.x & 31;
     const int ldp = a.ldp;
-    for (int k = 0; k < n; ++k) {
-        const T* __restrict__ row = a.SC + (size_t)list[k] * ldp;
-        for (int m = lane; m < n; m += 32) saa[k * BLK_AMAX + m] = row[list[m]];
-    }
     const int m0 = lane, m1 = lane + 32;
+    // S_AA, zero outside the n x n block so the idle slots stay finite; kept
+    // from the last phase when the support is the same (saa_list, saa_n)
+    const bool same = saa_n == n &&
+                      __all_sync(FULL_MASK, (m0 >= n || saa_list[m0] == list[m0]) &&
+                                                (m1 >= n || saa_list[m1] == list[m1]));
+    if (!same) {
+        const int l0 = m0 < n ? list[m0] : 0, l1 = m1 < n ? list[m1] : 0;
+        for (int k0 = 0; k0 < BLK_AMAX; k0 += 8) {
+            T v0[8], v1[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u;
+                const T* __restrict__ row = a.SC + (size_t)(k < n ? list[k] : 0) * ldp;
+                v0[u] = (k < n && m0 < n) ? row[l0] : T(0);
+                v1[u] = (k < n && m1 < n) ? row[l1] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                saa[(k0 + u) * BLK_AMAX + m0] = v0[u];
+                saa[(k0 + u) * BLK_AMAX + m1] = v1[u];
+            }
+        }
+        if (m0 < n) saa_list[m0] = list[m0];
+        if (m1 < n) saa_list[m1] = list[m1];
+        saa_n = n;
+        __syncwarp();
+    }
     const bool h0 = m0 < n, h1 = m1 < n;
     T b0 = h0 ? b[list[m0]] : T(0), b1 = h1 ? b[list[m1]] : T(0);
     T g0 = h0 ? a.SC[(size_t)j * ldp + list[m0]] : T(0);
@@ -1205,44 +1279,46 @@ __device__ int block_active_phase(int j, T* __restrict__ b, const int* __restric
     __syncwarp();
     for (int l = 0; l < n; ++l) {
         const T bl = __shfl_sync(FULL_MASK, l < 32 ? b0 : b1, l & 31);
-        if (h0) g0 = fma(-saa[l * BLK_AMAX + m0], bl, g0);
-        if (h1) g1 = fma(-saa[l * BLK_AMAX + m1], bl, g1);
+        g0 = fma(-saa[l * BLK_AMAX + m0], bl, g0);
+        g1 = fma(-saa[l * BLK_AMAX + m1], bl, g1);
     }
     conv = false;
     int sw = 0;
+    unsigned mv = 0;
     while (sw < a.maxit) {
         ++sw;
         T md = T(0);
+        T c0 = saa[m0], c1 = saa[m1];                     // column of S_AA for k = 0
         for (int k = 0; k < n; ++k) {
-            const int owner = k & 31;
+            const int kn = k + 1 < n ? k + 1 : k;
+            const T n0 = saa[kn * BLK_AMAX + m0], n1 = saa[kn * BLK_AMAX + m1];   // next column
             const bool hi = k >= 32;
-            T d = T(0), nb = T(0);
-            if (lane == owner) {
-                const T gk = hi ? g1 : g0, bk = hi ? b1 : b0;
-                if constexpr (STD) nb = soft<T>(gk + bk, lam);                  // S_kk = 1
-                else {
-                    const T sk = hi ? s1 : s0;
-                    nb = soft<T>(gk + sk * bk, lam) / sk;
-                }
-                d = nb - bk;
+            const T gk = hi ? g1 : g0, bk = hi ? b1 : b0;
+            T nb;
+            if constexpr (STD) {
+                nb = soft<T>(gk + bk, lam);                          // S_kk = 1
+            } else {
+                const T sk = hi ? s1 : s0;
+                nb = soft<T>(gk + sk * bk, lam) / sk;
             }
-            d = __shfl_sync(FULL_MASK, d, owner);
-            if (d != T(0)) {
-                if (h0) g0 = fma(-saa[k * BLK_AMAX + m0], d, g0);
-                if (h1) g1 = fma(-saa[k * BLK_AMAX + m1], d, g1);
-                if (lane == owner) {
-                    if (hi) b1 = nb;
-                    else b0 = nb;
-                }
-                md = fmax(md, fabs(d));
-                ++moves;
+            const T d = __shfl_sync(FULL_MASK, nb - bk, k & 31);
+            if (lane == (k & 31)) {
+                if (hi) b1 = nb;
+                else b0 = nb;
             }
+            g0 = fma(-c0, d, g0);
+            g1 = fma(-c1, d, g1);
+            md = fmax(md, fabs(d));
+            mv += d != T(0);
+            c0 = n0;
+            c1 = n1;
         }
         if ((double)md < a.tol) {
             conv = true;
             break;
         }
     }
+    moves += mv;
     if (h0) b[list[m0]] = b0;
     if (h1) b[list[m1]] = b1;
     return sw;
@@ -1264,15 +1340,27 @@ __device__ T block_sweep(int j, T* __restrict__ g, T* __restrict__ b, const CDAr
         const T* __restrict__ srow = a.SC + (size_t)(ks < 0 ? 0 : ks) * ldp;
         T* __restrict__ cb = cand + (size_t)par * 2 * BLK_THREADS;
         int kmin = INT_MAX;
-        for (int q = tid; 4 * q < ldp; q += BLK_THREADS) {
-            const int k0 = 4 * q;
+        // the thread's quads q0, q0 + BLK_THREADS, ... in groups of G, the
+        // group's S-row loads issued together
+        constexpr int G = sizeof(T) == 4 ? 4 : 2;
+        for (int q0 = tid; 4 * q0 < ldp; q0 += G * BLK_THREADS) {
+            T r[G][4];
+            if (ks >= 0) {
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    const int k0 = 4 * (q0 + u * BLK_THREADS);
+                    if (k0 < ldp) load4g<T>(srow + k0, r[u]);
+                }
+            }
+#pragma unroll
+          for (int u = 0; u < G; ++u) {
+            const int k0 = 4 * (q0 + u * BLK_THREADS);
+            if (k0 >= ldp) break;
             T gv[4];
             load4<T>(g + k0, gv);
             if (ks >= 0) {            // rank-1 update g -= S_.ks delta (Proposition 2)
-                T r[4];
-                load4g<T>(srow + k0, r);
 #pragma unroll
-                for (int t = 0; t < 4; ++t) gv[t] = fma(-delta, r[t], gv[t]);
+                for (int t = 0; t < 4; ++t) gv[t] = fma(-delta, r[u][t], gv[t]);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) g[k0 + t] = gv[t];
             }
@@ -1298,6 +1386,7 @@ __device__ T block_sweep(int j, T* __restrict__ g, T* __restrict__ b, const CDAr
                     }
                 }
             }
+          }
         }
         const int kb = block_min_int(kmin, sc, par);    // barrier: g updated, candidates visible
         if (kb == INT_MAX) break;
@@ -1361,6 +1450,8 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
     T* saa = b + ldp;
     int* list = reinterpret_cast<int*>(saa + BLK_AMAX * BLK_AMAX);
     T* cand = reinterpret_cast<T*>(list + BLK_LIST);
+    int* saa_list = reinterpret_cast<int*>(cand + 2 * 2 * BLK_THREADS);   // support of S_AA
+    int saa_n = -1;                                       // warp 0: no S_AA gathered yet
     int par = 0;
     {
         const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
@@ -1388,8 +1479,8 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
             if (n > 0 && n <= BLK_AMAX) {
                 int sw = 0;
                 bool c = false;
-                if (tid < 32) sw = block_active_phase<T, STD>(j, b, list, n, a, lam, saa,
-                                                              cnt.act_moves, c);
+                if (tid < 32) sw = block_active_phase<T, STD>(j, b, list, n, a, lam, saa, saa_list,
+                                                              saa_n, cnt.act_moves, c);
                 if (tid == 0) {
                     sc.red[par][0] = sw;
                     sc.red[par][1] = c ? 1 : 0;

@@ -139,6 +139,10 @@ __device__ __forceinline__ void set_error(FitCtrl* c, int code) { atomicCAS(&c->
 
 // Launchers implemented in the .cu files (host side, stream-ordered).
 namespace spmesl {
+// Heavy-column routing limits of spmesl_opts with the defaults applied.
+inline int heavy_heat_of(int v) { return v <= 0 ? 32 : (v > 62 ? 62 : v); }
+inline int heavy_min_p_of(int v) { return v == 0 ? 4096 : (v < 0 ? 0x7fffffff : v); }
+
 cudaError_t launch_gram(const void* X, int n, int p, int ldx, int precision, int center, void* S,
                         int lds, void* ws, cudaStream_t st);
 size_t gram_ws_bytes(int n, int p, int precision);
@@ -154,6 +158,8 @@ struct FitLaunch {
     unsigned char* ws;   // workspace base
     cudaEvent_t* phase_events;   // nullptr, or 3 events: before CD, after CD, after Theta
     int gradient;                // spmesl_gradient (column rule only)
+    int heavy_heat = 32;         // heat above which a column goes to the block solver
+    int heavy_min_p = 4096;      // ... in fits of at least this size (< 0: never)
     // >= 0: solve only this column (one scaled-lasso regression, lazy column
     // rule) and write its coefficients to beta_out (the p - 1 other columns in
     // order, original scale) and its sigma to sigma_out[0] instead of Theta

@@ -58,7 +58,7 @@ def test_metrics_deterministic():
 
 
 def test_table4_ar_rows():
-    """Means over the 50 datasets within 4.5 combined standard errors of the
+    """Means over the 50 datasets within 2.5 combined standard errors of the
     printed means (the printed values are rounded to 0.01) for |E|, SEN, SPE,
     FDR, MISR and MCC.  The Frobenius error within 3 % of the printed mean:
     its printed standard errors (about 0.01) are far below the differences
@@ -99,4 +99,4 @@ def test_table4_ar_rows():
                 continue
             s = max(math.hypot(se[i], row["se"][i]), fx["printed_resolution"])
             z = (mean[i] - row["mean"][i]) / s
-            assert abs(z) <= 4.5, (kind, row["method"], name, mean[i], row["mean"][i], z)
+            assert abs(z) <= 2.5, (kind, row["method"], name, mean[i], row["mean"][i], z)

@@ -214,16 +214,16 @@ def test_er_p2000_n200_fp32_full():
 @pytest.mark.parametrize("gradient", [sp.GRADIENT_AUTO, sp.GRADIENT_EAGER, sp.GRADIENT_LAZY])
 @pytest.mark.parametrize("prec,standardize", [("fp32", True), ("fp64", True), ("fp32", False)])
 def test_gradient_modes_match_oracle(gradient, prec, standardize):
-    """The hub network's hub columns have supports of about 50: with AUTO they
-    run on the block solver (routed by heat when standardised, handed over by
-    the lazy solver otherwise), with LAZY on the lazy solver alone."""
+    """The hub network's hub columns have large heat: with AUTO (heat routing
+    enabled at this size) they run on the block solver, with EAGER and LAZY
+    not at all."""
     dt = np.float64 if prec == "fp64" else np.float32
     tol = 1e-9 if prec == "fp64" else 1e-6
     prob = synth.make_problem("hub_scaled", 300, 140, 17, dtype=dt)
     Xd = torch.from_numpy(prob.X).to(DEV)
     S = sp.gram(Xd, precision=prec)
     T, sg, st = sp.fit(S, prob.lambda0, tol=tol, maxit=2000, precision=prec, gradient=gradient,
-                       standardize=standardize)
+                       standardize=standardize, heavy_min_p=1)
     assert st["status"] == sp.SPMESL_OK
     if gradient == sp.GRADIENT_AUTO and standardize:
         assert st["block_columns"] >= 10          # heat above 32: the hubs
@@ -233,19 +233,24 @@ def test_gradient_modes_match_oracle(gradient, prec, standardize):
     _assert_parity(T.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("n,p,seed", [(90, 257, 3), (200, 1000, 8)])
+@pytest.mark.parametrize("n,p,seed", [(90, 257, 3), (150, 400, 5)])
 def test_block_solver_batch_equals_single_fits(n, p, seed):
     """Heavy columns run on the block solver in a batch exactly as in a single
     fit: every Theta of a mixed batch of hub networks equals its single fit."""
     probs = [synth.make_problem("hub_scaled", p - 7 * i, n + 5 * i, seed + i, dtype=np.float32)
              for i in range(3)]
     inputs = [(torch.from_numpy(pr.X).to(DEV), pr.lambda0) for pr in probs]
-    bt = sp.Batch(inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000)
+    # heat routing for the two larger fits only: fits on both sides of heavy_min_p
+    bt = sp.Batch(inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000, heavy_min_p=p - 10)
     bt.run()
     statuses, st = bt.result()
     assert all(s == sp.SPMESL_OK for s in statuses) and st["block_columns"] > 0
     for i, pr in enumerate(probs):
-        _, T, sg, _, _ = _gpu_fit(pr.X, pr.lambda0, 1e-6, 1000, "fp32")
+        Xd = torch.from_numpy(np.ascontiguousarray(pr.X)).to(DEV)
+        S = sp.gram(Xd, precision="fp32")
+        Td, sgd, _ = sp.fit(S, pr.lambda0, tol=1e-6, maxit=1000, precision="fp32",
+                            heavy_min_p=p - 10)
+        T, sg = Td.cpu().numpy(), sgd.cpu().numpy()
         assert np.array_equal(bt.Theta[i].cpu().numpy(), T)
         assert np.array_equal(bt.sigma[i].cpu().numpy(), sg)
     bt.close()

@@ -2,7 +2,7 @@
 the seeded datasets per row (p = 500, n = 250), the paper's three penalty
 levels, the measures of oracle.support_metrics.  This pins the oracle, the
 sampling of X and the measures to values the paper prints: |E|, SEN, SPE,
-FDR, MISR and MCC within 4.5 combined standard errors (ours from the 20
+FDR, MISR and MCC within 2.5 combined standard errors (ours from the 20
 datasets, the paper's from its 50), the Frobenius error within 3 % (its
 printed standard errors are far below what unstated details of the paper's
 computation move it by)."""
@@ -51,4 +51,4 @@ def test_table4_ar_rows_with_the_oracle():
                 continue
             s = max(math.hypot(se[i], row["se"][i]), fx["printed_resolution"])
             z = (mean[i] - row["mean"][i]) / s
-            assert abs(z) <= 4.5, (kind, row["method"], name, mean[i], row["mean"][i], z)
+            assert abs(z) <= 2.5, (kind, row["method"], name, mean[i], row["mean"][i], z)
