@@ -114,7 +114,8 @@ typedef struct {
     int32_t heavy_min_p;        /* ... only in fits with p >= heavy_min_p (0 = 4096; < 0: never).
                                    In any fit a column whose support outgrows the lazy solver's
                                    32-coordinate active-set phase is handed over to it */
-    int32_t reserved[4];
+    int32_t count_rows;         /* measurement: 1 fills spmesl_stats.rows_moved */
+    int32_t reserved[3];
 } spmesl_opts;
 
 typedef struct {
@@ -152,6 +153,10 @@ typedef struct {
                                    exact estimator: the first-order effect of the measured
                                    gradient residuals and sigma fixed-point residuals, plus the
                                    rounding bound of the working matrix (see spmesl_opts) */
+    int64_t rows_moved;         /* opts.count_rows: for each full-sweep index m (the m-th full
+                                   sweep of a column, m < 64), the number of distinct coordinates
+                                   k that moved in sweep m of any column, summed over m: the rows
+                                   of S a row-synchronous schedule reads for its rank-1 updates */
 } spmesl_stats;
 
 /* A helper (no passage of the paper): fill `opts` with the defaults: FP32,
@@ -251,7 +256,7 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
  *   commits the 64 MiB on the device, and the device holds it until the
  *   process exits.  Make that first call at start-up, and before any stream
  *   capture.  If the device has no room for the array, SPMESL_ENOMEM.
- *   Size limit: the fit's scratch must fit in 64 MiB, i.e. p <= 2352 for
+ *   Size limit: the fit's scratch must fit in 64 MiB, i.e. p <= 2351 for
  *   SPMESL_FP32 / SPMESL_MIXED and p <= 1664 for SPMESL_FP64; larger p returns
  *   SPMESL_ENOMEM before any work is enqueued.
  *   All calls share the array and it keeps the last call's contents (each fit
@@ -316,6 +321,38 @@ spmesl_status spmesl_fit_residual(const void* X, int n, int p, int ldx, double l
  * device buffer, original scale, B[j*p + k] = b_jk, zero diagonal). */
 spmesl_status spmesl_fit_coefficients(const void* workspace, int p, int precision, double* B,
                                       void* stream);
+
+/*
+ * Optimality check of an estimate (Section 2.1: the scaled-lasso optimality
+ * conditions of each column problem of Eq. (5); Eq. (14)): for every column k
+ * of B, with lambda = lambda0 sigma_k on the working matrix (S^C when
+ * opts->standardize, else S) and g = S_.k - S b_k formed in FP64 on the device,
+ *   kkt_viol  = max over k and j != k of |g_j - lambda sign(b_jk)| (b_jk != 0)
+ *               or (|g_j| - lambda)_+ (b_jk = 0), divided by lambda;
+ *   dual_gap  = max over k of (P - D) / P of the lasso subproblem, with
+ *               rr = S_kk - b'S_.k - b'g, yr = S_kk - b'S_.k,
+ *               s = min(1, lambda / ||g||_inf), P = rr / 2 + lambda ||b||_1,
+ *               D = s yr - s^2 rr / 2;
+ *   err_est   = the first-order estimate of max |dTheta| / max |Theta| that
+ *               these residuals and the sigma fixed-point residual imply, with
+ *               the rounding bound of a working matrix built in
+ *               opts->precision from n samples added (spmesl_stats).
+ * The same check runs after a fit with opts->diagnostics = 1.  The paper has
+ * no such routine; it defines the conditions checked.
+ *   S       p x p covariance as for spmesl_fit (read only).
+ *   n       sample size for the rounding bound (and lambda rules); 0 = 1.
+ *   B       p x p FP64 coefficients in the original scale, B[j*p + k] = b_jk
+ *           (the layout of spmesl_fit_coefficients); sigma: p FP64 values.
+ *   stats   host, required: status, lambda0, diagnostics = 1, kkt_viol,
+ *           dual_gap and err_est are written; the call synchronises `stream`.
+ *   workspace  spmesl_fit_workspace_bytes(p, precision), 256-byte aligned.
+ * Errors: EINVAL (NULL pointers, p < 2 or above spmesl_max_p, short or
+ * misaligned workspace, no usable lambda0), ENONFINITE (non-finite S or
+ * S_jj <= 0), ECUDA.
+ */
+spmesl_status spmesl_diagnose(const void* S, int n, int p, double lambda0, const double* B,
+                              const double* sigma, const spmesl_opts* opts, spmesl_stats* stats,
+                              void* workspace, size_t ws_bytes, void* stream);
 
 /*
  * One scaled-lasso regression (Section 2.1, Eq. (2); Algorithm 1): the joint
@@ -457,6 +494,14 @@ spmesl_status spmesl_batch_run(spmesl_batch* batch, void* workspace, size_t ws_b
  * (may be NULL).  Returns the most severe status. */
 spmesl_status spmesl_batch_result(const spmesl_batch* batch, const void* workspace,
                                   int32_t* statuses, spmesl_stats* stats, void* stream);
+
+/* A helper (no passage of the paper): the counters of fit i (caller's order)
+ * from the last spmesl_batch_result:
+ * status, sweeps, moves, nonzero coefficients, the block solver's columns, the
+ * penalty level and, with opts.diagnostics, the fit's kkt_viol / dual_gap /
+ * err_est (the aggregate of spmesl_batch_result gives their maxima).  Host
+ * only.  EINVAL for a bad index, ENOTFOUND before the first result. */
+spmesl_status spmesl_batch_fit_stats(const spmesl_batch* batch, int i, spmesl_stats* stats);
 
 /* Autotune (not in the paper) warps per block of the batch's
  * coordinate-descent launch (Algorithm 1 per column) by timing

@@ -25,12 +25,14 @@ __all__ = [
     "spmesl_default_opts", "spmesl_status_string", "spmesl_version", "spmesl_lambda",
     "spmesl_max_p", "spmesl_gram_workspace_bytes", "spmesl_gram", "spmesl_fit_workspace_bytes",
     "spmesl_fit", "spmesl_fit_noalloc", "spmesl_fit_result", "spmesl_fit_coefficients",
+    "spmesl_diagnose", "diagnose",
     "spmesl_fit_residual_workspace_bytes", "spmesl_fit_residual",
     "spmesl_scaled_lasso_workspace_bytes", "spmesl_scaled_lasso",
     "spmesl_metrics_workspace_bytes", "spmesl_support_metrics",
     "spmesl_solve_workspace_bytes",
     "spmesl_solve", "spmesl_batch_create", "spmesl_batch_workspace_bytes", "spmesl_batch_run",
-    "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_destroy", "Problem", "Batch",
+    "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_fit_stats", "spmesl_batch_destroy",
+    "Problem", "Batch",
     "spmesl_ctx_create", "spmesl_submit", "spmesl_poll", "spmesl_ctx_query", "spmesl_ctx_destroy",
     "Server",
     "gram", "fit", "fit_residual", "solve",
@@ -53,7 +55,7 @@ class Opts(ctypes.Structure):
                 ("record_phase_times", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("gradient", ctypes.c_int32), ("diagnostics", ctypes.c_int32),
                 ("heavy_heat", ctypes.c_int32), ("heavy_min_p", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("count_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Problem(ctypes.Structure):
@@ -75,7 +77,8 @@ class Stats(ctypes.Structure):
                 ("reserved32", ctypes.c_int32), ("active_sweeps", ctypes.c_int64),
                 ("active_moves", ctypes.c_int64), ("block_columns", ctypes.c_int32),
                 ("diagnostics", ctypes.c_int32), ("kkt_viol", ctypes.c_double),
-                ("dual_gap", ctypes.c_double), ("err_est", ctypes.c_double)]
+                ("dual_gap", ctypes.c_double), ("err_est", ctypes.c_double),
+                ("rows_moved", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
@@ -121,6 +124,8 @@ _SIGS = {
                                    ctypes.POINTER(Opts), _vp, _vp, ctypes.POINTER(Stats), _vp,
                                    _sz, _vp]),
     "spmesl_fit_coefficients": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "spmesl_diagnose": (_i32, [_vp, _i32, _i32, _dbl, _vp, _vp, ctypes.POINTER(Opts),
+                               ctypes.POINTER(Stats), _vp, _sz, _vp]),
     "spmesl_scaled_lasso_workspace_bytes": (_sz, [_i32, _i32, _i32]),
     "spmesl_metrics_workspace_bytes": (_sz, []),
     "spmesl_support_metrics": (_i32, [_vp, _vp, _i32, ctypes.POINTER(Metrics), _vp, _sz, _vp]),
@@ -133,6 +138,7 @@ _SIGS = {
     "spmesl_batch_result": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(Stats), _vp]),
     "spmesl_batch_tune": (_i32, [_vp, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "spmesl_batch_fit_stats": (_i32, [_vp, _i32, ctypes.POINTER(Stats)]),
     "spmesl_batch_destroy": (None, [_vp]),
     "spmesl_ctx_create": (_i32, [ctypes.POINTER(ctypes.c_void_p), _sz, _i32, _dbl, _i32,
                                  ctypes.POINTER(Opts)]),
@@ -282,6 +288,31 @@ def spmesl_fit_result(workspace, p, precision, stats, stream=None) -> int:
 
 def spmesl_fit_coefficients(workspace, p, precision, B, stream=None) -> int:
     return lib().spmesl_fit_coefficients(_ptr(workspace), p, precision, _ptr(B), _stream(stream))
+
+
+def spmesl_diagnose(S, n, p, lambda0, B, sigma, opts, stats, workspace, ws_bytes,
+                    stream=None) -> int:
+    return lib().spmesl_diagnose(_ptr(S), n, p, lambda0, _ptr(B), _ptr(sigma),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.byref(stats), _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def diagnose(S, lambda0, B, sigma, n=0, precision="fp32", standardize=True, stream=None) -> dict:
+    """Optimality diagnostics (kkt_viol, dual_gap, err_est) of an estimate
+    (B, sigma) in the original scale against the CUDA covariance S."""
+    _require_cuda()
+    prec = _prec(precision)
+    p = S.shape[0]
+    opts = spmesl_default_opts()
+    opts.precision = prec
+    opts.standardize = int(bool(standardize))
+    nb = spmesl_fit_workspace_bytes(p, prec)
+    keep, ws = _workspace(nb, S.device)
+    st = Stats()
+    _check(spmesl_diagnose(S.contiguous(), n, p, lambda0, B.contiguous(), sigma.contiguous(), opts,
+                           st, ws, nb, stream), "spmesl_diagnose")
+    del keep
+    return st.as_dict()
 
 
 def spmesl_scaled_lasso_workspace_bytes(n: int, p: int, precision: int) -> int:
@@ -478,6 +509,10 @@ def spmesl_batch_tune(batch, workspace, ws_bytes, stream=None) -> tuple[int, int
     return rc, w.value
 
 
+def spmesl_batch_fit_stats(batch, i, stats) -> int:
+    return lib().spmesl_batch_fit_stats(batch, int(i), ctypes.byref(stats))
+
+
 def spmesl_batch_destroy(batch) -> None:
     lib().spmesl_batch_destroy(batch)
 
@@ -492,7 +527,7 @@ class Batch:
     def __init__(self, inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000,
                  use_graph=False, warps_per_block=0, center=False, record_phase_times=False,
                  gradient=GRADIENT_AUTO, heavy_heat=0, heavy_min_p=0, diagnostics=False,
-                 device=None):
+                 count_rows=False, device=None):
         import torch
         _require_cuda()
         prec = _prec(precision)
@@ -524,6 +559,7 @@ class Batch:
         opts.heavy_heat = int(heavy_heat)
         opts.heavy_min_p = int(heavy_min_p)
         opts.diagnostics = int(bool(diagnostics))
+        opts.count_rows = int(bool(count_rows))
         rc, self.handle = spmesl_batch_create(arr, self.count, tol, maxit, opts)
         _check(rc, "spmesl_batch_create")
         self.ws_bytes = spmesl_batch_workspace_bytes(self.handle)
@@ -542,6 +578,12 @@ class Batch:
         statuses = (ctypes.c_int32 * self.count)()
         spmesl_batch_result(self.handle, self.ws, statuses, st, stream)
         return list(statuses), st.as_dict()
+
+    def fit_stats(self, i: int) -> dict:
+        """Counters (and diagnostics) of fit i from the last result()."""
+        st = Stats()
+        _check(spmesl_batch_fit_stats(self.handle, i, st), "spmesl_batch_fit_stats")
+        return st.as_dict()
 
     def close(self):
         if getattr(self, "handle", None):

@@ -91,6 +91,28 @@ void read_phase_times(const void* ws, spmesl_stats* stats) {
     cudaGetLastError();
 }
 
+double from_bits(unsigned long long b) {
+    double d;
+    memcpy(&d, &b, sizeof(d));
+    return d;
+}
+
+}  // namespace
+
+namespace spmesl {
+// The diagnostics of a control block into the stats (when they were computed).
+void fill_diagnostics(const FitCtrl& c, spmesl_stats* stats) {
+    if (c.diag_cols == 0 || !stats) return;
+    stats->diagnostics = 1;
+    stats->kkt_viol = from_bits(c.diag_kkt);
+    stats->dual_gap = from_bits(c.diag_gap);
+    const double th = from_bits(c.diag_thmax);
+    stats->err_est = th > 0.0 ? from_bits(c.diag_err) / th : NAN;
+}
+}  // namespace spmesl
+
+namespace {
+
 spmesl_opts resolve_opts(const spmesl_opts* o) {
     spmesl_opts d;
     spmesl_default_opts(&d);
@@ -238,6 +260,9 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
     f.gradient = o.gradient;
     f.heavy_heat = o.heavy_heat;
     f.heavy_min_p = o.heavy_min_p;
+    f.diagnostics = o.diagnostics ? 1 : 0;
+    f.diag_eps = diag_eps_for(o.precision, n);
+    f.count_rows = o.count_rows ? 1 : 0;
     f.Theta = Theta;
     f.sigma_out = sigma;
     f.ws = static_cast<unsigned char*>(workspace);
@@ -379,6 +404,8 @@ spmesl_status spmesl_scaled_lasso(const void* X, const void* y, int n, int p, do
         f.gradient = SPMESL_GRADIENT_AUTO;
         f.heavy_heat = o.heavy_heat;
         f.heavy_min_p = o.heavy_min_p;
+        f.diagnostics = o.diagnostics ? 1 : 0;
+        f.diag_eps = diag_eps_for(o.precision, n);
         f.Theta = nullptr;
         f.sigma_out = sigma;
         f.ws = ws + L.fit;
@@ -434,6 +461,8 @@ spmesl_status spmesl_fit_result(const void* workspace, int p, int precision, spm
         stats->max_col_sweeps = c.max_col_sweeps;
         stats->max_col_outer = c.outer_max;
         stats->block_columns = c.block_cols;
+        stats->rows_moved = (int64_t)c.rows_moved;
+        fill_diagnostics(c, stats);
         read_phase_times(workspace, stats);
     }
     return s;
@@ -444,6 +473,38 @@ spmesl_status spmesl_fit_coefficients(const void* workspace, int p, int precisio
     if (!workspace || !B || p < 2 || !valid_precision(precision)) return SPMESL_EINVAL;
     return from_cuda(launch_export_B(static_cast<const unsigned char*>(workspace), p, precision, B,
                                      static_cast<cudaStream_t>(stream)));
+}
+
+spmesl_status spmesl_diagnose(const void* S, int n, int p, double lambda0, const double* B,
+                              const double* sigma, const spmesl_opts* opts, spmesl_stats* stats,
+                              void* workspace, size_t ws_bytes, void* stream) {
+    const spmesl_opts o = resolve_opts(opts);
+    if (!S || !B || !sigma || !stats || !workspace || p < 2 || !valid_precision(o.precision))
+        return SPMESL_EINVAL;
+    if (p > max_p_for(o.precision)) return SPMESL_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return SPMESL_EINVAL;
+    if (ws_bytes < fit_layout(p, o.precision).total) return SPMESL_EINVAL;
+    double lam = lambda0;
+    if (o.lambda_rule != SPMESL_LAMBDA_GIVEN) lam = spmesl_lambda(o.lambda_rule, n, p);
+    if (!(lam > 0.0) || !isfinite(lam)) return SPMESL_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_diagnose(S, p, o.precision, o.standardize ? 1 : 0, lam, B, sigma,
+                                    diag_eps_for(o.precision, n),
+                                    static_cast<unsigned char*>(workspace), st);
+    if (e != cudaSuccess) return from_cuda(e);
+    FitCtrl c;
+    e = cudaMemcpyAsync(&c, workspace, sizeof(FitCtrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    memset(stats, 0, sizeof(*stats));
+    stats->lambda0 = lam;
+    if (c.err == DEV_ERR_NONFINITE) {
+        stats->status = SPMESL_ENONFINITE;
+        return SPMESL_ENONFINITE;
+    }
+    fill_diagnostics(c, stats);
+    stats->status = SPMESL_OK;
+    return SPMESL_OK;
 }
 
 size_t spmesl_solve_workspace_bytes(int n, int p, int precision) {

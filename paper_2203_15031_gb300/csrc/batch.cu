@@ -46,6 +46,8 @@ struct BatchFit {
     void* XlT;
     float* cmax;          // first-sweep chunk maxima of the lazy solver (standardised fits)
     double lambda0;
+    double diag_eps;      // rounding bound of the working matrix (diagnostics)
+    unsigned* rows;       // moved-coordinate bitmap of the fit (opts.count_rows) or nullptr
     int n, p, ldp;
     int col_start, gram_start, theta_start;
     int split_start;      // first block of the batched split/transpose launch
@@ -188,7 +190,16 @@ __device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, 
     a.n_queue = f.p;
     a.ovf_supp = ovf_supp;
     a.chunk_max = f.cmax;
+    a.rows_moved = f.rows;
+    a.rows_words = rows_words(f.p);
     return a;
+}
+
+// Distinct moved coordinates of every fit (opts.count_rows): one block per fit.
+__global__ void batch_rows_count_kernel(const BatchFit* __restrict__ fits) {
+    const BatchFit& f = fits[blockIdx.x];
+    if (f.rows)
+        count_rows_moved(f.rows, rows_bitmap_bytes(f.p) / 4, f.ctrl, threadIdx.x, blockDim.x);
 }
 
 // Eager gradient over all columns of all fits, or (from_queue) over the
@@ -303,6 +314,28 @@ __global__ void __launch_bounds__(BLK_THREADS, 1) batch_cd_block_kernel(const Ba
     }
 }
 
+// Optimality diagnostics of every column of every fit (opts.diagnostics):
+// one warp per column, 4 warps a block, grid-stride over the columns.
+constexpr int BATCH_DIAG_WARPS = 4;
+template <typename T>
+__global__ void __launch_bounds__(32 * BATCH_DIAG_WARPS) batch_diag_kernel(
+    const BatchFit* __restrict__ fits, const int* __restrict__ col_prefix, int count,
+    int total_cols) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char* wsm = smem_raw + (size_t)warp * diag_warp_smem_bytes();
+    for (int gc = blockIdx.x * BATCH_DIAG_WARPS + warp; gc < total_cols;
+         gc += gridDim.x * BATCH_DIAG_WARPS) {
+        const int fi = find_fit(col_prefix, count, gc);
+        const BatchFit& f = fits[fi];
+        if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) continue;
+        const CDArgs<T> a = column_args<T>(f, 0.0, 1);
+        DiagMax d;
+        diagnose_column<T>(gc - f.col_start, wsm, a, f.diag_eps, d);
+        flush_diag(f.ctrl, d);
+    }
+}
+
 // Zero every fit's Theta (what = 0) or coefficient rows BT (what = 1;
 // elem bytes per element), with 16-byte stores where aligned.  Both run on
 // a side stream: BT under the Gram and the standardisation (the
@@ -354,7 +387,7 @@ struct FitPlan {
     double* Theta;
     double* sigma;
     size_t off_ctrl, off_cs, off_csf, off_sigma, off_status, off_diag, off_cmax, off_mu, off_Sg, off_SC,
-        off_BT;
+        off_BT, off_rows;
     size_t off_XhT, off_XlT;
     int col_start, gram_start, theta_start, split_start, prep_start;
 };
@@ -396,12 +429,16 @@ struct spmesl_batch {
     int warps_per_block = 0;       // 0 = automatic
     int gradient = SPMESL_GRADIENT_AUTO;
     int heavy_heat = 0, heavy_min_p = 0;   // routing limits of spmesl_opts (0: defaults)
+    int diagnostics = 0;           // optimality diagnostics after the coordinate descent
+    mutable std::vector<spmesl_stats> fit_stats;   // per fit, caller's order (last result)
     size_t off_ovf = 0;            // queue of columns for the eager launch (total_cols ints)
     size_t off_heat = 0, off_order = 0;   // per-column heat and the lazy queue's order
     std::vector<FitPlan> plan;     // ordered by decreasing p
     size_t off_hdr = 0, off_desc = 0, off_colp = 0, off_gramp = 0, off_thetap = 0, off_ctrls = 0;
     size_t off_prepp = 0;          // block prefix of the standardisation launch
     int total_prep = 0;
+    int count_rows = 0;            // moved-coordinate bitmaps (measurement)
+    size_t off_rows = 0, rows_bytes = 0;   // all fits' bitmaps, contiguous
     // SPMESL_MIXED: tensor-core Gram table, fit of every tile, split prefixes
     size_t off_tcfit = 0, off_tilefit = 0, off_splitp = 0;
     int total_split = 0;
@@ -445,6 +482,9 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
         return e;
     if ((e = cudaMemsetAsync(ws + b->off_hdr, 0, sizeof(BatchHeader), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws + b->off_ctrls, 0, (size_t)256 * b->count, st)) != cudaSuccess)
+        return e;
+    if (b->count_rows &&
+        (e = cudaMemsetAsync(ws + b->off_rows, 0, b->rows_bytes, st)) != cudaSuccess)
         return e;
     const int count = b->count;
     // fork: Theta is zeroed on the side stream while the fits run
@@ -555,6 +595,17 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
                                           b->maxit, hdr, ovf, 0);
     }
     if (timed) cudaEventRecord(b->ev[1], st);
+    if (b->count_rows) batch_rows_count_kernel<<<count, 256, 0, st>>>(fits);
+    if (b->diagnostics) {
+        const size_t dsm = diag_warp_smem_bytes() * BATCH_DIAG_WARPS;
+        auto dk = batch_diag_kernel<T>;
+        if ((e = cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)dsm)) != cudaSuccess)
+            return e;
+        const int dgrid = std::max(1, std::min((b->total_cols + BATCH_DIAG_WARPS - 1) / BATCH_DIAG_WARPS,
+                                               num_sms() * 4));
+        dk<<<dgrid, 32 * BATCH_DIAG_WARPS, dsm, st>>>(fits, colp, count, b->total_cols);
+    }
     if ((e = cudaStreamWaitEvent(st, b->join, 0)) != cudaSuccess) return e;   // join
     batch_theta_kernel<T><<<b->total_theta, dim3(32, 8), 0, st>>>(fits, thetap, count);
     return cudaGetLastError();
@@ -606,6 +657,8 @@ bool stage_table(spmesl_batch* b, unsigned char* ws) {
         d.sigma_out = f.sigma;
         d.ctrl = reinterpret_cast<FitCtrl*>(ws + f.off_ctrl);
         d.lambda0 = f.lambda0;
+        d.diag_eps = diag_eps_for(b->precision, f.X ? f.n : 1);
+        d.rows = b->count_rows ? reinterpret_cast<unsigned*>(ws + f.off_rows) : nullptr;
         d.n = f.n;
         d.p = f.p;
         d.ldp = f.ldp;
@@ -686,6 +739,8 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->gradient = o.gradient;
     b->heavy_heat = o.heavy_heat;
     b->heavy_min_p = o.heavy_min_p;
+    b->diagnostics = o.diagnostics ? 1 : 0;
+    b->count_rows = o.count_rows ? 1 : 0;
     b->tol = tol;
     b->maxit = maxit;
     std::vector<int> order(count);
@@ -772,6 +827,14 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->total_split = split;
     b->total_theta = theta;
     b->total_prep = prep;
+    if (b->count_rows) {
+        b->off_rows = off;
+        for (FitPlan& f : b->plan) {
+            f.off_rows = off;
+            off += align_up(rows_bitmap_bytes(f.p), 256);
+        }
+        b->rows_bytes = off - b->off_rows;
+    }
     b->off_ovf = off;
     off += align_up(sizeof(int) * (size_t)cols, 256);
     b->off_heat = off;
@@ -877,11 +940,34 @@ spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, 
     spmesl_status worst = SPMESL_OK;
     spmesl_stats agg;
     memset(&agg, 0, sizeof(agg));
+    b->fit_stats.assign(b->count, agg);
     for (const FitPlan& f : b->plan) {
         FitCtrl c;
         memcpy(&c, ctrls.data() + (f.off_ctrl - b->off_ctrls), sizeof(c));
         const spmesl_status s = status_of(c);
         if (statuses) statuses[f.src] = s;
+        spmesl_stats& fs = b->fit_stats[f.src];
+        fs.status = s;
+        fs.outer_iters = c.outer_max;
+        fs.inner_sweeps = (int64_t)c.total_sweeps;
+        fs.moves = (int64_t)c.moves;
+        fs.active_sweeps = (int64_t)c.act_sweeps;
+        fs.active_moves = (int64_t)c.act_moves;
+        fs.nnz_B = (int64_t)c.nnz;
+        fs.n_not_converged = c.n_not_converged;
+        fs.n_degenerate = c.n_degenerate;
+        fs.max_col_sweeps = c.max_col_sweeps;
+        fs.max_col_outer = c.outer_max;
+        fs.block_columns = c.block_cols;
+        fs.rows_moved = (int64_t)c.rows_moved;
+        fs.lambda0 = f.lambda0;
+        fill_diagnostics(c, &fs);
+        if (fs.diagnostics) {
+            agg.diagnostics = 1;
+            agg.kkt_viol = std::max(agg.kkt_viol, fs.kkt_viol);
+            agg.dual_gap = std::max(agg.dual_gap, fs.dual_gap);
+            agg.err_est = std::max(agg.err_est, fs.err_est);
+        }
         if (s < 0 && (worst >= 0 || s < worst)) worst = s;
         else if (s > 0 && worst == SPMESL_OK) worst = s;
         agg.outer_iters = std::max(agg.outer_iters, c.outer_max);
@@ -895,6 +981,7 @@ spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, 
         agg.max_col_sweeps = std::max(agg.max_col_sweeps, c.max_col_sweeps);
         agg.max_col_outer = std::max(agg.max_col_outer, c.outer_max);
         agg.block_columns += c.block_cols;
+        agg.rows_moved += (int64_t)c.rows_moved;
     }
     agg.status = worst;
     if (b->ev_recorded) {
@@ -903,6 +990,13 @@ spmesl_status spmesl_batch_result(const spmesl_batch* b, const void* workspace, 
     }
     if (stats) *stats = agg;
     return worst;
+}
+
+spmesl_status spmesl_batch_fit_stats(const spmesl_batch* b, int i, spmesl_stats* stats) {
+    if (!b || !stats || i < 0 || i >= b->count) return SPMESL_EINVAL;
+    if ((int)b->fit_stats.size() != b->count) return SPMESL_ENOTFOUND;   // no result read yet
+    *stats = b->fit_stats[i];
+    return SPMESL_OK;
 }
 
 spmesl_status spmesl_batch_tune(spmesl_batch* b, void* workspace, size_t ws_bytes, void* stream,

@@ -118,6 +118,43 @@ __global__ void __launch_bounds__(BLK_THREADS, 1) cd_column_block_kernel(CDArgs<
     flush_counters_block(ctrl, cnt);
 }
 
+__global__ void rows_count_kernel(const unsigned* __restrict__ bits, size_t nwords, FitCtrl* ctrl) {
+    count_rows_moved(bits, nwords, ctrl, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+                     (size_t)gridDim.x * blockDim.x);
+}
+
+// Optimality diagnostics of columns [j0, j1): one warp per column
+// (diagnose_column), 4 warps a block, grid-stride over the columns.
+constexpr int DIAG_WARPS = 4;
+template <typename T>
+__global__ void __launch_bounds__(32 * DIAG_WARPS) cd_diag_kernel(CDArgs<T> a, double eps, int j0,
+                                                                  int j1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char* wsm = smem_raw + (size_t)warp * diag_warp_smem_bytes();
+    if (*reinterpret_cast<volatile int*>(&a.ctrl->err) != 0) return;
+    DiagMax d;
+    for (int j = j0 + blockIdx.x * DIAG_WARPS + warp; j < j1; j += gridDim.x * DIAG_WARPS)
+        diagnose_column<T>(j, wsm, a, eps, d);
+    flush_diag(a.ctrl, d);
+}
+
+// A caller's estimate in the original scale onto the working scale of the
+// workspace (spmesl_diagnose): BT[k][j] = b^C_jk = b_jk c_k / c_j (the
+// inverse of the map of Proposition 1's proof) and sigma^C_k = sigma_k c_k.
+template <typename T>
+__global__ void load_estimate_kernel(const double* __restrict__ B, const double* __restrict__ sig,
+                                     int p, int ldp, const double* __restrict__ cs,
+                                     T* __restrict__ BT, double* __restrict__ sigma_w) {
+    const size_t total = (size_t)p * p;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i / p), k = (int)(i - (size_t)j * p);   // B[j][k] = b_jk
+        BT[(size_t)k * ldp + j] = j == k ? T(0) : (T)(B[i] * cs[k] / cs[j]);
+        if (j == 0) sigma_w[k] = sig[k] * cs[k];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Joint rule (Algorithm 3): all active columns sweep together; a sweep ends at
 // a grid barrier where max_{active j} ||b_j,next - b_j,cur||_inf is tested.
@@ -236,7 +273,7 @@ __global__ void __launch_bounds__(512) cd_joint_kernel(CDArgs<T> a) {
                 ColScan cs{reinterpret_cast<ChunkInfo*>(list + SUPP_CAP), 0.f, 0u};
                 reset_chunks(cs, a.ldp);
                 __syncwarp();
-                wmax = fmax(wmax, sweep_column<T, STD>(j, g, b, a, lam, moves, cs));
+                wmax = fmax(wmax, sweep_column<T, STD>(j, g, b, a, lam, moves, cs, (int)gs));
                 if (!resident) {
                     warp_copy<T>(a.GT + (size_t)j * a.ldp, g, a.ldp);
                     warp_copy<T>(a.BT + (size_t)j * a.ldp, b, a.ldp);
@@ -501,6 +538,18 @@ static cudaError_t block_launch_shape(int ldp, size_t& smem, int& grid) {
     return cudaSuccess;
 }
 
+template <typename T>
+static cudaError_t launch_diag(const CDArgs<T>& a, double eps, int j0, int j1, cudaStream_t st) {
+    const size_t sm = diag_warp_smem_bytes() * DIAG_WARPS;
+    auto k = cd_diag_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int cols = j1 - j0;
+    const int grid = std::max(1, std::min((cols + DIAG_WARPS - 1) / DIAG_WARPS, g_num_sms * 4));
+    k<<<grid, 32 * DIAG_WARPS, sm, st>>>(a, eps, j0, j1);
+    return cudaGetLastError();
+}
+
 template <typename T, bool STD>
 static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t st) {
     cudaError_t e = device_limits();
@@ -528,6 +577,8 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     a.order = nullptr;
     a.n_queue = f.p;
     a.chunk_max = nullptr;
+    a.rows_moved = f.count_rows ? reinterpret_cast<unsigned*>(ws + L.rows) : nullptr;
+    a.rows_words = rows_words(f.p);
     const bool single = f.response_col >= 0;    // one regression: lazy column rule
     const bool joint = !single && f.inner_rule == SPMESL_INNER_JOINT;
     // Lazy launch shape (warps per block, blocks per SM).
@@ -572,6 +623,9 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     if (heat && (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)f.p, st)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(ws + L.BT, 0, (size_t)f.p * L.ldp * sizeof(T), st)) != cudaSuccess)
+        return e;
+    if (a.rows_moved &&
+        (e = cudaMemsetAsync(a.rows_moved, 0, rows_bitmap_bytes(f.p), st)) != cudaSuccess)
         return e;
     const int pb = 256;
     prep_diag_kernel<T><<<(f.p + pb - 1) / pb, pb, 0, st>>>(
@@ -671,6 +725,12 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (f.phase_events) cudaEventRecord(f.phase_events[1], st);
+    if (a.rows_moved)
+        rows_count_kernel<<<g_num_sms, 256, 0, st>>>(a.rows_moved, rows_bitmap_bytes(f.p) / 4, ctrl);
+    if (f.diagnostics) {
+        const int j0 = single ? f.response_col : 0, j1 = single ? f.response_col + 1 : f.p;
+        if ((e = launch_diag<T>(a, f.diag_eps, j0, j1, st)) != cudaSuccess) return e;
+    }
 
     if (single) {
         lasso_export_kernel<T><<<(f.p + 255) / 256, 256, 0, st>>>(
@@ -693,6 +753,51 @@ cudaError_t launch_fit(const FitLaunch& f, cudaStream_t st) {
         return f.standardize ? run_fit<double, true>(f, L, st) : run_fit<double, false>(f, L, st);
     }
     return f.standardize ? run_fit<float, true>(f, L, st) : run_fit<float, false>(f, L, st);
+}
+
+template <typename T>
+static cudaError_t run_diagnose(const void* S, int p, int standardize, double lambda0,
+                                const double* B, const double* sigma, double eps,
+                                unsigned char* ws, const FitLayout& L, cudaStream_t st) {
+    cudaError_t e = device_limits();
+    if (e != cudaSuccess) return e;
+    FitCtrl* ctrl = reinterpret_cast<FitCtrl*>(ws + L.ctrl);
+    double* cs = reinterpret_cast<double*>(ws + L.cs);
+    CDArgs<T> a{};
+    a.SC = reinterpret_cast<const T*>(ws + L.SC);
+    a.BT = reinterpret_cast<T*>(ws + L.BT);
+    a.diag = reinterpret_cast<const T*>(ws + L.diag);
+    a.sigma = reinterpret_cast<double*>(ws + L.sigma);
+    a.ctrl = ctrl;
+    a.p = p;
+    a.ldp = L.ldp;
+    a.lambda0 = lambda0;
+    if ((e = cudaMemsetAsync(ctrl, 0, sizeof(FitCtrl), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws + L.BT, 0, (size_t)p * L.ldp * sizeof(T), st)) != cudaSuccess)
+        return e;
+    const int pb = 256;
+    prep_diag_kernel<T><<<(p + pb - 1) / pb, pb, 0, st>>>(
+        reinterpret_cast<const T*>(S), p, standardize, cs, reinterpret_cast<float*>(ws + L.csf),
+        a.sigma, reinterpret_cast<int*>(ws + L.active), reinterpret_cast<int*>(ws + L.col_status),
+        ctrl);
+    prep_matrix_kernel<T><<<std::min(p, g_num_sms * 8), pb, 0, st>>>(
+        reinterpret_cast<const T*>(S), p, L.ldp, cs, reinterpret_cast<const float*>(ws + L.csf),
+        reinterpret_cast<T*>(ws + L.SC), nullptr, reinterpret_cast<T*>(ws + L.diag), 0, ctrl, T(0),
+        nullptr, nullptr);
+    const size_t total = (size_t)p * p;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)g_num_sms * 16);
+    load_estimate_kernel<T><<<grid, 256, 0, st>>>(B, sigma, p, L.ldp, cs, a.BT, a.sigma);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_diag<T>(a, eps, 0, p, st);
+}
+
+cudaError_t launch_diagnose(const void* S, int p, int precision, int standardize,
+                            double lambda0, const double* B, const double* sigma, double eps,
+                            unsigned char* ws, cudaStream_t st) {
+    const FitLayout L = fit_layout(p, precision);
+    if (precision == SPMESL_FP64)
+        return run_diagnose<double>(S, p, standardize, lambda0, B, sigma, eps, ws, L, st);
+    return run_diagnose<float>(S, p, standardize, lambda0, B, sigma, eps, ws, L, st);
 }
 
 cudaError_t launch_export_B(const unsigned char* ws, int p, int precision, double* B,

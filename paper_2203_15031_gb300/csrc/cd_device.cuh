@@ -33,7 +33,30 @@ struct CDArgs {
     const float* chunk_max;   // per column j and 128-coordinate chunk c, max_k |S^C_jk| over
                               // the chunk (k != j), written by the standardisation pass; the
                               // first sweep's skip test starts from it (nullptr: scan all)
+    unsigned* rows_moved;     // measurement (nullptr: off): bit k of row m is set when
+                              // coordinate k moved in the m-th full sweep of any column
+    int rows_words;           // 32-bit words per row of that bitmap
 };
+
+// Full sweeps per column whose moved coordinates are recorded in the bitmap.
+constexpr int ROWS_SWEEPS = 64;
+
+// ctrl->rows_moved += the set bits of bits[0, nwords) (grid-stride).
+__device__ __forceinline__ void count_rows_moved(const unsigned* __restrict__ bits, size_t nwords,
+                                                 FitCtrl* ctrl, size_t tid, size_t nthr) {
+    unsigned long long c = 0;
+    for (size_t i = tid; i < nwords; i += nthr) c += __popc(bits[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL_MASK, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctrl->rows_moved, c);
+}
+
+// Record that coordinate k moved in full sweep m (one thread calls it).
+template <typename T>
+__device__ __forceinline__ void note_row_moved(const CDArgs<T>& a, int m, int k) {
+    if (a.rows_moved && m >= 0 && m < ROWS_SWEEPS)
+        atomicOr(a.rows_moved + (size_t)m * a.rows_words + (k >> 5), 1u << (k & 31));
+}
 
 namespace {
 // Order of a coordinate-descent queue: columns by decreasing heat (the count
@@ -220,7 +243,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 template <typename T, bool STD>
 __device__ T sweep_column(int j, T* __restrict__ g, T* __restrict__ b, const CDArgs<T>& a, T lam,
-                          unsigned long long& moves, ColScan& cs) {
+                          unsigned long long& moves, ColScan& cs, int sweep_idx = -1) {
     const int lane = threadIdx.x & 31;
     const int p = a.p;
     const int ldp = a.ldp;
@@ -268,7 +291,10 @@ __device__ T sweep_column(int j, T* __restrict__ g, T* __restrict__ b, const CDA
             const T nbs = __shfl_sync(FULL_MASK, nb_sel, f);
             const T delta = nbs - __shfl_sync(FULL_MASK, b_sel, f);
             const int ks = cb + f * SCAN_V + tf;
-            if (lane == 0) b[ks] = nbs;
+            if (lane == 0) {
+                b[ks] = nbs;
+                note_row_moved(a, sweep_idx, ks);
+            }
             maxd = fmax(maxd, fabs(delta));
             ++moves;
             cs.dsum += fabsf((float)delta);
@@ -558,7 +584,8 @@ __device__ void solve_column(int j, T* __restrict__ g, T* __restrict__ b, int* _
         const T lam = (T)(sigma * a.lambda0);
         bool inner_ok = false;
         for (int m = 0; m < a.maxit; ++m) {
-            const T md = sweep_column<T, STD>(j, g, b, a, lam, cnt.moves, cs);
+            const T md = sweep_column<T, STD>(j, g, b, a, lam, cnt.moves, cs,
+                                              (int)(cnt.sweeps - sweeps0));
             ++cnt.sweeps;
             if ((double)md < a.tol) {
                 inner_ok = true;
@@ -717,7 +744,7 @@ __device__ __forceinline__ unsigned chunks_to_scan(const ColScan& cs, int from, 
 template <typename T, bool STD>
 __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
                                unsigned long long& moves, ColScan& cs, bool& overflow,
-                               bool frozen) {
+                               bool frozen, int sweep_idx) {
     const int lane = threadIdx.x & 31;
     const int p = a.p;
     const int ldp = a.ldp;
@@ -813,6 +840,7 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
                 return maxd;
             }
             e1 += s.n - n_before;
+            if (lane == 0) note_row_moved(a, sweep_idx, ks);
             if (lane == f) {
 #pragma unroll
                 for (int u = 0; u < SCAN_V; ++u)
@@ -1005,7 +1033,8 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
             bool conv;
             if (s.n > a.ovf_supp) return false;          // a heavy column: the block solver
             cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.act_moves, cs, conv);
-            const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow, conv);
+            const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow, conv,
+                                                   (int)(cnt.sweeps - sweeps0));
             ++cnt.sweeps;
             if (overflow) return false;
             if ((double)md < a.tol) {
@@ -1057,6 +1086,171 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
     cnt.n_deg += (status & COL_DEGENERATE) != 0;
     __syncwarp();
     return true;
+}
+
+// ===========================================================================
+// Optimality diagnostics of a finished fit (opts.diagnostics).
+//
+// For column j the returned pair (b_j, sigma_j) solves Algorithm 1's problem
+// when the lasso subgradient conditions hold at lambda = lambda0 sigma_j
+// (Section 2.1): with g = S_.j - S b_j,
+//   g_k = lambda sign(b_k) where b_k != 0,   |g_k| <= lambda where b_k = 0,
+// and sigma_j is the fixed point of Eq. (14).  One warp per column forms the
+// whole gradient in FP64 from the working matrix (row j and the support rows,
+// the lazy solver's slices accumulated in FP64) and reports
+//  - the largest violation of those conditions relative to lambda;
+//  - the relative duality gap (P - D) / P of the lasso subproblem: with
+//    rr = S_jj - b'S_.j - b'g (= ||x_j - X b||^2 / n), yr = S_jj - b'S_.j and
+//    the dual point s r, s = min(1, lambda / ||g||_inf):
+//    P = rr / 2 + lambda ||b||_1, D = s yr - s^2 rr / 2;
+//  - a first-order estimate of the error of the column's Theta entries.  The
+//    rounding of the working matrix (eps_s per entry, relative) moves each
+//    gradient entry by about eps_s (1 + ||b||_2) (independent signs); with
+//    the measured gradient residual this is read as a coefficient error
+//    (unit diagonal).  sigma moves by the fixed-point residual plus
+//    drr / (2 sigma), drr the first-order change of rr: eps_s (1 + ||b||_2)^2
+//    from the matrix (at the optimum the change through b is second order)
+//    and 2 lambda |A| kkt from a solve that is not exactly optimal.  Then
+//    Theta_kj = -b_kj / sigma_j^2, Theta_jj = 1 / sigma_j^2 differentiated.
+// ===========================================================================
+constexpr int DIAG_CAP = 1024;         // support list of one warp
+
+__host__ __device__ constexpr size_t diag_warp_smem_bytes() {
+    return (size_t)DIAG_CAP * (sizeof(int) + sizeof(double));
+}
+
+// Per-warp maxima of the diagnostics (non-negative doubles), flushed with
+// atomicMax on their bits.
+struct DiagMax {
+    double kkt = 0.0, gap = 0.0, err = 0.0, thmax = 0.0;
+};
+
+__device__ __forceinline__ void flush_diag(FitCtrl* ctrl, const DiagMax& d) {
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&ctrl->diag_kkt, dbits(d.kkt));
+        atomicMax(&ctrl->diag_gap, dbits(d.gap));
+        atomicMax(&ctrl->diag_err, dbits(d.err));
+        atomicMax(&ctrl->diag_thmax, dbits(d.thmax));
+        atomicAdd(&ctrl->diag_cols, 1u);
+    }
+}
+
+template <typename T>
+__device__ void diagnose_column(int j, unsigned char* wsm, const CDArgs<T>& a, double eps_s,
+                                DiagMax& out) {
+    const int lane = threadIdx.x & 31;
+    const int p = a.p, ldp = a.ldp;
+    int* idx = reinterpret_cast<int*>(wsm);
+    double* val = reinterpret_cast<double*>(wsm + DIAG_CAP * sizeof(int));
+    const T* __restrict__ brow = a.BT + (size_t)j * ldp;
+    // support of b_j in ascending order
+    int ns = 0;
+    for (int c0 = 0; c0 < p; c0 += 32) {
+        const int k = c0 + lane;
+        const T bk = k < p ? brow[k] : T(0);
+        const unsigned bal = __ballot_sync(FULL_MASK, bk != T(0));
+        const int pos = ns + __popc(bal & ((1u << lane) - 1u));
+        if (bk != T(0) && pos < DIAG_CAP) {
+            idx[pos] = k;
+            val[pos] = (double)bk;
+        }
+        ns += __popc(bal);
+    }
+    __syncwarp();
+    const bool listed = ns <= DIAG_CAP;
+    const double sig = a.sigma[j];
+    const double lam = a.lambda0 * sig;
+    const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
+    double kkt = 0.0, gmax = 0.0, bg = 0.0;
+    for (int cb = 0; cb < p; cb += CHUNK) {
+        const int k0 = cb + lane * SCAN_V;
+        const bool in = k0 < ldp;
+        double acc[SCAN_V] = {0.0, 0.0, 0.0, 0.0};
+        if (in) {
+            T r[SCAN_V];
+            load4g<T>(Sj + k0, r);
+#pragma unroll
+            for (int t = 0; t < SCAN_V; ++t) acc[t] = (double)r[t];
+        }
+        if (listed) {
+#pragma unroll 4
+            for (int e = 0; e < ns; ++e) {
+                const double v = val[e];
+                if (in) {
+                    T r[SCAN_V];
+                    load4g<T>(a.SC + (size_t)idx[e] * ldp + k0, r);
+#pragma unroll
+                    for (int t = 0; t < SCAN_V; ++t) acc[t] = fma(-v, (double)r[t], acc[t]);
+                }
+            }
+        } else {
+            for (int l = 0; l < p; ++l) {
+                const double v = (double)brow[l];
+                if (v != 0.0 && in) {
+                    T r[SCAN_V];
+                    load4g<T>(a.SC + (size_t)l * ldp + k0, r);
+#pragma unroll
+                    for (int t = 0; t < SCAN_V; ++t) acc[t] = fma(-v, (double)r[t], acc[t]);
+                }
+            }
+        }
+        if (in) {
+            T bq[SCAN_V];
+            load4g<T>(brow + k0, bq);
+#pragma unroll
+            for (int t = 0; t < SCAN_V; ++t) {
+                const int k = k0 + t;
+                if (k >= p || k == j) continue;
+                const double g = acc[t], bk = (double)bq[t];
+                const double viol = bk != 0.0 ? fabs(g - copysign(lam, bk)) : fmax(0.0, fabs(g) - lam);
+                kkt = fmax(kkt, viol);
+                gmax = fmax(gmax, fabs(g));
+                if (bk != 0.0) bg = fma(bk, g, bg);
+            }
+        }
+    }
+    double bS = 0.0, l1 = 0.0, l2 = 0.0, bmax = 0.0;
+    if (listed) {
+        for (int e = lane; e < ns; e += 32) {
+            bS = fma(val[e], (double)Sj[idx[e]], bS);
+            l1 += fabs(val[e]);
+            l2 = fma(val[e], val[e], l2);
+            bmax = fmax(bmax, fabs(val[e]));
+        }
+    } else {
+        for (int k = lane; k < p; k += 32) {
+            const double v = (double)brow[k];
+            bS = fma(v, (double)Sj[k], bS);
+            l1 += fabs(v);
+            l2 = fma(v, v, l2);
+            bmax = fmax(bmax, fabs(v));
+        }
+    }
+    kkt = warp_max(kkt);
+    gmax = warp_max(gmax);
+    bmax = warp_max(bmax);
+    bg = warp_sum(bg);
+    bS = warp_sum(bS);
+    l1 = warp_sum(l1);
+    l2 = sqrt(warp_sum(l2));
+    const double Sjj = (double)Sj[j];
+    const double rr = Sjj - bS - bg;
+    const double yr = Sjj - bS;
+    const double s = gmax > lam ? lam / gmax : 1.0;
+    const double P = 0.5 * rr + lam * l1;
+    const double D = s * yr - 0.5 * s * s * rr;
+    const double gap = P > 0.0 ? fmax(0.0, P - D) / P : 0.0;
+    // first-order error of the column's Theta entries
+    const double eb = kkt + eps_s * (1.0 + l2);
+    const double es = fabs(sig - sqrt(fmax(rr, 0.0))) +
+                      (eps_s * (1.0 + l2) * (1.0 + l2) + 2.0 * lam * (double)ns * kkt) / (2.0 * sig);
+    const double s2 = sig * sig;
+    const double eth = eb / s2 + 2.0 * fmax(1.0, bmax) * es / (s2 * sig);
+    out.kkt = fmax(out.kkt, lam > 0.0 ? kkt / lam : kkt);
+    out.gap = fmax(out.gap, gap);
+    out.err = fmax(out.err, eth);
+    out.thmax = fmax(out.thmax, 1.0 / s2);
+    __syncwarp();
 }
 
 // ===========================================================================
@@ -1330,7 +1524,7 @@ __device__ int block_active_phase(int j, T* __restrict__ b, const int* __restric
 template <typename T, bool STD>
 __device__ T block_sweep(int j, T* __restrict__ g, T* __restrict__ b, const CDArgs<T>& a, T lam,
                          bool frozen, T* __restrict__ cand, unsigned long long& moves,
-                         BlockScratch& sc, int& par) {
+                         BlockScratch& sc, int& par, int sweep_idx) {
     const int tid = threadIdx.x;
     const int p = a.p, ldp = a.ldp;
     T maxd = T(0);
@@ -1392,7 +1586,10 @@ __device__ T block_sweep(int j, T* __restrict__ g, T* __restrict__ b, const CDAr
         if (kb == INT_MAX) break;
         const int owner = (kb >> 2) % BLK_THREADS;      // the thread whose quads hold kb
         delta = cb[BLK_THREADS + owner];
-        if (tid == owner) b[kb] = cb[owner];
+        if (tid == owner) {
+            b[kb] = cb[owner];
+            note_row_moved(a, sweep_idx, kb);
+        }
         maxd = fmax(maxd, fabs(delta));
         ++moves;
         ks = kb;
@@ -1493,7 +1690,8 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
                 block_form_gradient<T>(j, g, b, list, n, a);
                 __syncthreads();
             }
-            const T md = block_sweep<T, STD>(j, g, b, a, lam, conv, cand, cnt.moves, sc, par);
+            const T md = block_sweep<T, STD>(j, g, b, a, lam, conv, cand, cnt.moves, sc, par,
+                                             (int)(cnt.sweeps - sweeps0));
             ++cnt.sweeps;
             if ((double)md < a.tol) {
                 inner_ok = true;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "spmesl.h"
@@ -47,6 +48,15 @@ struct FitCtrl {
     int pad[1];
     unsigned long long act_sweeps;     // lazy solver: sweeps over the support only
     unsigned long long act_moves;      // moves in those sweeps
+    // optimality diagnostics (opts.diagnostics): maxima over the columns of
+    // the relative subgradient violation, the relative duality gap, the
+    // first-order Theta error estimate and 1/sigma^2 (bits of non-negative
+    // doubles), and the columns checked
+    unsigned long long diag_kkt, diag_gap, diag_err, diag_thmax;
+    unsigned int diag_cols;
+    unsigned int pad2;
+    unsigned long long rows_moved;     // measurement (opts.count_rows): distinct coordinates
+                                       // moved per full-sweep index, summed over the indices
 };
 static_assert(sizeof(FitCtrl) <= 256, "FitCtrl must fit its 256-byte slot");
 
@@ -62,12 +72,17 @@ inline int padded_ld(int p) { return (p + 31) / 32 * 32; }
 // Byte offsets of the fit workspace (see spmesl_fit_workspace_bytes).
 struct FitLayout {
     int ldp;
-    size_t ctrl, cs, csf, sigma, col_status, active, active_next, flag, diag, cmax, SC, BT, GT,
-        total;
+    size_t ctrl, cs, csf, sigma, col_status, active, active_next, flag, diag, cmax, rows, SC, BT,
+        GT, total;
 };
 
 // 128-coordinate chunks of a padded row (the lazy solver's scan unit).
 inline int row_chunks(int ldp) { return (ldp + 127) / 128; }
+
+// Bitmap of the coordinates moved per full-sweep index (opts.count_rows):
+// 64 rows of ceil(p / 32) words.
+__host__ __device__ inline int rows_words(int p) { return (p + 31) / 32; }
+__host__ __device__ inline size_t rows_bitmap_bytes(int p) { return (size_t)64 * rows_words(p) * 4; }
 
 inline FitLayout fit_layout(int p, int precision) {
     FitLayout L{};
@@ -85,6 +100,7 @@ inline FitLayout fit_layout(int p, int precision) {
     L.flag = off;        off += align_up((size_t)p * 4, 256);
     L.diag = off;        off += align_up((size_t)p * s, 256);
     L.cmax = off;        off += align_up((size_t)p * row_chunks(L.ldp) * 4, 256);
+    L.rows = off;        off += align_up(rows_bitmap_bytes(p), 256);
     L.SC = off;          off += mat;
     L.BT = off;          off += mat;
     L.GT = off;          off += mat;
@@ -160,6 +176,9 @@ struct FitLaunch {
     int gradient;                // spmesl_gradient (column rule only)
     int heavy_heat = 32;         // heat above which a column goes to the block solver
     int heavy_min_p = 4096;      // ... in fits of at least this size (< 0: never)
+    int diagnostics = 0;         // 1: optimality diagnostics after the coordinate descent
+    int count_rows = 0;          // 1: count the distinct coordinates moved per sweep index
+    double diag_eps = 0.0;       // rounding bound of the working matrix (see diag_eps_for)
     // >= 0: solve only this column (one scaled-lasso regression, lazy column
     // rule) and write its coefficients to beta_out (the p - 1 other columns in
     // order, original scale) and its sigma to sigma_out[0] instead of Theta
@@ -167,6 +186,24 @@ struct FitLaunch {
     double* beta_out = nullptr;
 };
 cudaError_t launch_fit(const FitLaunch& f, cudaStream_t st);
+// Diagnostics of a given (B, sigma) in the original scale against S (spmesl_diagnose).
+cudaError_t launch_diagnose(const void* S, int p, int precision, int standardize,
+                            double lambda0, const double* B, const double* sigma, double eps,
+                            unsigned char* ws, cudaStream_t st);
+// Typical rounding of an entry of a working matrix built in `precision` from
+// n samples, relative to sqrt(S_jj S_kk): two roundings of the
+// standardisation, the accumulation of the Gram over n terms (sqrt(n) unit
+// roundoffs, the usual size of a sum of independent roundings), and for
+// SPMESL_MIXED the 3-term split-BF16 products (each within 3 * 2^-18 of the
+// exact product: hi and lo of a factor keep 16 bits, lo * lo is dropped),
+// averaged over the n products (/ sqrt(n)).  An estimate, not a bound.
+inline double diag_eps_for(int precision, int n) {
+    const double u = precision == SPMESL_FP64 ? 0x1p-53 : 0x1p-24;
+    const double rn = sqrt((double)(n > 1 ? n : 1));
+    double e = u * (2.0 + rn);
+    if (precision == SPMESL_MIXED) e += 3.0 * 0x1p-18 / rn;
+    return e;
+}
 // One fit in the residual form (residual.cu): X n x p (ld ldx) on the device.
 struct ResLaunch {
     const void* X;
@@ -183,6 +220,7 @@ cudaError_t launch_fit_residual(const ResLaunch& f, cudaStream_t st);
 bool residual_sizes_ok(int n, int p, int precision);
 cudaError_t launch_export_B(const unsigned char* ws, int p, int precision, double* B,
                             cudaStream_t st);
+void fill_diagnostics(const FitCtrl& c, spmesl_stats* stats);
 int max_p_for(int precision);
 
 // When true on the calling thread, spmesl_batch_create stages its descriptor

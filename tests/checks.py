@@ -181,3 +181,45 @@ def compare_theta(T_gpu: np.ndarray, T_ref: np.ndarray, B_ref: np.ndarray, sigma
     return dict(ok=(nbad == 0 and not supp_mismatch.any()), max_abs_err=float(err.max()),
                 max_rel_err=float(err.max() / scale), n_bad=nbad,
                 n_support_mismatch=int(supp_mismatch.sum()), scale=scale)
+
+
+def diagnostics_host(S: np.ndarray, B: np.ndarray, sigma: np.ndarray, lambda0: float,
+                     standardize: bool = True):
+    """The optimality diagnostics of an estimate, restated on the host in
+    FP64: per column k, on the working scale (B and sigma in the ORIGINAL
+    scale), lambda = lambda0 sigma_k and g = W_.k - W b_k:
+      subgradient violation relative to lambda (b_jk != 0: |g_j - lambda
+      sign b_jk|; b_jk = 0: (|g_j| - lambda)_+), and the relative duality gap
+      (P - D)/P of the lasso at lambda, with the dual point s (x_k - X b_k),
+      s = min(1, lambda / ||g||_inf): P = rr/2 + lambda ||b||_1,
+      D = s yr - s^2 rr / 2, rr = ||x_k - X b_k||^2 / n = W_kk - 2 b'W_.k + b'W b,
+      yr = x_k'(x_k - X b_k) / n = W_kk - b'W_.k.
+    Returns (max violation, max relative gap)."""
+    p = S.shape[0]
+    c = 1.0 / np.sqrt(np.diag(S)) if standardize else np.ones(p)
+    W = S * c[:, None] * c[None, :]
+    Bc = B * c[None, :] / c[:, None]
+    sc = sigma * c
+    viol, gap = 0.0, 0.0
+    for k in range(p):
+        b = Bc[:, k].copy()
+        b[k] = 0.0
+        lam = lambda0 * sc[k]
+        g = W[:, k] - W @ b
+        others = np.arange(p) != k
+        nz = (b != 0) & others
+        z = (b == 0) & others
+        v = 0.0
+        if nz.any():
+            v = max(v, float(np.max(np.abs(g[nz] - lam * np.sign(b[nz])))))
+        if z.any():
+            v = max(v, float(np.max(np.maximum(np.abs(g[z]) - lam, 0.0))))
+        viol = max(viol, v / lam)
+        rr = W[k, k] - 2 * b @ W[:, k] + b @ W @ b
+        yr = W[k, k] - b @ W[:, k]
+        gmax = float(np.max(np.abs(g[others])))
+        s = min(1.0, lam / gmax) if gmax > 0 else 1.0
+        P = rr / 2 + lam * np.sum(np.abs(b))
+        D = s * yr - s * s * rr / 2
+        gap = max(gap, max(0.0, P - D) / P)
+    return viol, gap

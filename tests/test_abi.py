@@ -166,3 +166,12 @@ def test_every_entry_point_cites_its_passage():
                 block = last
             assert cite.search(block), m.group(1)
             prev, last = text.index(";", m.end()) + 1, block
+
+
+def test_noalloc_limits_match_the_fit_workspace():
+    """The allocation-free fit's documented limits are the largest p whose fit
+    workspace fits its 64 MiB scratch (include/spmesl.h)."""
+    cap = 64 << 20
+    for prec, limit in ((sp.FP32, 2351), (sp.MIXED, 2351), (sp.FP64, 1664)):
+        assert sp.spmesl_fit_workspace_bytes(limit, prec) <= cap
+        assert sp.spmesl_fit_workspace_bytes(limit + 1, prec) > cap
