@@ -1,35 +1,47 @@
-"""Benchmark: SPMESL solves/s on one GB300 (and N replicas under torchrun).
+"""Benchmark: SPMESL solves/s and latency on one GB300 (and N replicas under torchrun).
 
-Workload (default): Erdos-Renyi network, p = 2000, n = 200, X float32 with
-rows N(0, Theta^{-1}), lambda0 = sqrt(2 log p / n), tol 1e-6, maxit 1000.  One
-step is one pass of the whole path over a batch of ten datasets (seeds 0..9,
-resident in HBM) through the batched C ABI in mixed precision: split-BF16
-Gram S = X'X/n on the tensor cores, standardisation, FP32 coordinate descent
-with FP64 sigma updates, Theta assembly and symmetrisation in FP64, one launch
-per phase for all ten fits.  The same batch with the FP32 Gram and the plain
-path (one FP32 spmesl_gram + spmesl_fit per fit, serialised on one stream) are
-timed beside it.
+Default workload (batch256): 256 independent SPMESL fits, fit i drawn with
+seed 1000 + i: p log-uniform in [50, 2000], n uniform in [30, 400], the network
+AR(1) / Erdos-Renyi / hub at random, X float32 with rows N(0, Theta^{-1}),
+lambda0 = sqrt(2 log p / n), tol 1e-6, maxit 1000.  One step is one replay of
+the batch's captured CUDA graph in mixed precision: split-BF16 Gram on the
+tensor cores for all 256 fits, standardisation, FP32 coordinate descent (lazy
+solver, block solver for the columns it hands over) with FP64 sigma updates,
+Theta assembly and symmetrisation in FP64.  Inputs are resident in HBM; L2 is
+flushed (256 MB write) between steps and the flush is outside the step's
+events.
 
 JSON line fields beyond the base contract:
-  e2e          the same metric through the batched C ABI with HOST buffers (the
-               ten X copied in from pinned memory, every Theta and sigma copied
-               out, inside the timed region), with the device-to-host link
-               measured in the same run and the ceiling it sets
-  plain        solves/s of the one-fit-per-launch path on the same ten datasets
-  batched_fp32 the same batch with the FP32 Gram on the CUDA cores
-  accuracy     max |dTheta| / max |Theta| against the plain path and the oracle
-  roofline     the coordinate-descent launch: algorithmic bytes per launch over
-               its CUDA-event duration, against the measured HBM copy bandwidth;
-               sweep_model gives the bytes of the row-synchronous G schedule
-  cpu_baseline the FP64 oracle on the host cores, on a bounded sample
-  latency      p50 / p99 of the per-solve device time
+  plain        the same 256 fits one FP32 spmesl_gram + spmesl_fit per fit,
+               serialised on one stream: solves/s and per-solve latency
+  latency      p50 / p99 of the batched step (every solve of a step completes
+               with it) and of the plain per-fit solves
+  served       the serving workload: Poisson arrivals of requests (p
+               log-uniform in [100, 5000], n = max(p/4, 50)) into the serving
+               context (continuous batching, mixed precision) against the plain
+               path fed the same arrivals, at 0.5 and 0.9 of the served
+               saturation rate; saturation measured three times (spread given)
+  er_p2000_x10 ten ER p=2000 n=200 fits as one mixed batch (the single-shape batch)
+  accuracy     max|dTheta|/max|Theta| of the batched mixed results against the
+               FP64 oracle on every fit of the step, and the largest
+               err_est / kkt_viol / dual_gap the device diagnostics state
+  e2e          the same batch through the C ABI with host buffers: every X
+               copied in from pinned memory and every Theta and sigma copied out
+               inside the timed region, two batches on two streams in turn
+  roofline     the coordinate-descent launches of a step (the dominant kernels):
+               the row-synchronous byte model of the coordinate descent over
+               their CUDA-event time against the measured HBM copy bandwidth;
+               the per-column model beside it
+  cpu_baseline the FP64 oracle (Gram + Algorithm 2) on the step's 256 fits on all
+               host cores, and on as many as 20 s allow on one core; Gram and
+               fit timed apart
   clocks       SM clocks and throttle reasons sampled during the timed region
 
 --impl reference times the FP64 CPU oracle (the only reference this method
-has) on the same workload and prints its line with "impl": "reference".
---workload names another measurement: a single fit of synth.WORKLOADS (for
-example hub_p10000_n500_mixed), batch256, serve, regression, table4 or
-residual.
+has) on a sample of the same workload and prints its line with
+"impl": "reference".  --workload names another measurement: a single fit of
+synth.WORKLOADS (for example hub_p10000_n500_mixed), er10 (the ten-fit batch
+alone), serve, regression, table4 or residual.
 """
 from __future__ import annotations
 
@@ -47,16 +59,18 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SPMESL solves/s + p99 latency, mixed-prec batched vs plain GPU @ dTheta<=1e-4"
-WORKLOAD = "er_p2000_n200_fp32"
-N_DATASETS = 10
-# the headline batched path: split-BF16 Gram on the tensor cores, CD in FP32,
-# sigma / convergence / Theta in FP64
+WORKLOAD = "batch256"
+N_FITS = 256
 BATCH_PREC = "mixed"
-# per batched step: coefficient-row and Theta zeroing (side stream), split/transpose,
-# tcgen05 Gram, prep_diag, prep_matrix, column order, lazy cd, eager cd queue,
-# theta (the FP32 path has one SIMT Gram launch instead of the split and the
-# tcgen05 Gram)
-KERNELS_PER_SOLVE = {"mixed": 10, "fp32": 9}
+TOL, MAXIT = 1e-6, 1000
+# kernels of one batched mixed step: coefficient-row and Theta zeroing (side
+# stream), split/transpose, tcgen05 Gram, prep_diag, prep_matrix, column order,
+# block solver over the heavy columns (second side stream), lazy solver,
+# block solver over the handed-over columns, Theta
+KERNELS_PER_STEP = 11
+# fits of the batch the oracle solves (accuracy, CPU baseline, reference arm)
+ORACLE_SAMPLE = list(range(N_FITS))
+REFERENCE_SAMPLE = list(range(0, N_FITS, 32))
 
 
 def _env_rank():
@@ -145,63 +159,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs(count: int):
-    import numpy as np
-    import synth
-    w = synth.WORKLOADS[WORKLOAD]
-    probs = [synth.make_problem(w["kind"], w["p"], w["n"], s, dtype=np.float32)
-             for s in range(count)]
-    return w, probs
-
-
-def cpu_baseline(w, prob, budget_s: float = 20.0, theta_gpu=None):
-    """FP64 oracle (as it stands) on the host cores: one whole solve (Gram +
-    Algorithm 2) of dataset seed 0, repeated while it stays inside the budget.
-    With theta_gpu (the GPU's Theta of the same dataset) it also returns
-    max|dTheta| / max|Theta| of that result against the oracle's."""
-    import numpy as np
-    import oracle
-    oracle.build()
-    cores = os.cpu_count() or 1
-    X64 = prob.X.astype(np.float64)
-    times = []
-    t_start = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        S = oracle.gram(X64)
-        ref = oracle.spmesl(S, prob.lambda0, tol=w["tol"], maxit=w["maxit"], nthreads=cores)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > budget_s or len(times) >= 5:
-            break
-    t = statistics.median(times)
-    out = {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
-           "sample": f"{len(times)} whole solves (FP64 Gram + Algorithm 2, OpenMP over columns) "
-                     f"of the ER p={prob.p} n={prob.n} dataset seed 0, median {t:.3f} s"}
-    if theta_gpu is not None:
-        T = ref["Theta"]
-        out["gpu_max_rel_dtheta"] = float(np.max(np.abs(theta_gpu - T)) / np.max(np.abs(T)))
-    return out
-
-
-def run_reference(args):
-    rank, _, world = _env_rank()
-    if rank != 0:
-        return
-    w, probs = make_inputs(1)
-    cb = cpu_baseline(w, probs[0], budget_s=max(5.0, 3.0 * args.steps))
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "solves/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "p": probs[0].p, "n": probs[0].n,
-                       "network": "erdos_renyi", "lambda0": "sqrt(2 log p / n)",
-                       "tol": w["tol"], "maxit": w["maxit"]},
-            "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 def _sha_of(paths):
     """sha256 of the sources with comments and whitespace removed, so that a
     profile stays attached to the code it measured across comment edits."""
@@ -217,27 +174,110 @@ def _sha_of(paths):
     return h.hexdigest()
 
 
+
+
+# ----------------------------------------------------------------------------- workloads
+def batch_problems(only=None):
+    """The 256 fits of the batched workload (synth.batch_specs, seeds 1000 + i);
+    with `only`, just those fits (None in the other places)."""
+    import numpy as np
+    import synth
+    keep = set(range(N_FITS)) if only is None else set(only)
+    return [synth.make_problem(s["kind"], s["p"], s["n"], s["seed"], dtype=np.float32)
+            if i in keep else None for i, s in enumerate(synth.batch_specs(N_FITS))]
+
+
+def oracle_sample(probs, idx, nthreads: int, budget_s: float | None = None):
+    """The FP64 oracle (Gram, then Algorithm 2) on the fits idx, in order,
+    stopping once budget_s is spent: wall time of the Gram and of the fit
+    summed over the fits done, and their Thetas."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    t_gram = t_fit = 0.0
+    thetas = {}
+    t0 = time.perf_counter()
+    for i in idx:
+        X = probs[i].X.astype(np.float64)
+        a = time.perf_counter()
+        S = oracle.gram(X)
+        b = time.perf_counter()
+        ref = oracle.spmesl(S, probs[i].lambda0, tol=TOL, maxit=MAXIT, nthreads=nthreads)
+        c = time.perf_counter()
+        t_gram += b - a
+        t_fit += c - b
+        thetas[i] = ref["Theta"]
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    return dict(fits=len(thetas), t_gram=t_gram, t_fit=t_fit, thetas=thetas)
+
+
+def cpu_baseline(probs, budget_single_s: float = 20.0):
+    """The oracle as it stands on the host cores: the sampled fits on all
+    cores (OpenMP over columns), then on one core within a time budget."""
+    cores = os.cpu_count() or 1
+    allc = oracle_sample(probs, ORACLE_SAMPLE, cores)
+    one = oracle_sample(probs, ORACLE_SAMPLE, 1, budget_s=budget_single_s)
+    ps = [probs[i].p for i in ORACLE_SAMPLE]
+    out = {"value": allc["fits"] / (allc["t_gram"] + allc["t_fit"]), "unit": "solves/s",
+           "cores": cores, "kind": "oracle",
+           "sample": f"all {allc['fits']} fits of one step (p {min(ps)}-{max(ps)}): FP64 Gram, "
+                     f"then Algorithm 2 with OpenMP over columns on all cores",
+           "gram_s": allc["t_gram"], "fit_s": allc["t_fit"],
+           "single_thread": {"value": one["fits"] / (one["t_gram"] + one["t_fit"]),
+                             "unit": "solves/s", "cores": 1, "fits": one["fits"],
+                             "gram_s": one["t_gram"], "fit_s": one["t_fit"],
+                             "sample": f"the first {one['fits']} fits of the same step, one "
+                                       f"thread, within {budget_single_s:.0f} s"}}
+    return out, allc["thetas"]
+
+
+def rel_err(T, R) -> float:
+    import numpy as np
+    return float(np.max(np.abs(T - R)) / np.max(np.abs(R)))
+
+
+# ----------------------------------------------------------------------------- byte models
+def gschedule_bytes(s: int, fits) -> float:
+    """Bytes of the row-synchronous schedule with G in memory (coordinate
+    descent written on G = S - S B), summed over fits given as dicts of p and
+    the device counters: every column sweep reads its p entries of G, every
+    coordinate change reads and writes a column of G, every distinct
+    coordinate moved in a sweep index reads one row of S, and B is written."""
+    b = 0.0
+    for f in fits:
+        b += s * f["p"] * (f["inner_sweeps"] + 2.0 * f["moves"] + f["rows_moved"]) + 2.0 * s * f["nnz_B"]
+    return b
+
+
+def column_bytes(s: int, fits) -> float:
+    """Per-column model of the lazy solver: each column reads S_.j and writes
+    b_j, each full-sweep move reads one row of S."""
+    b = 0.0
+    for f in fits:
+        ldp = (f["p"] + 31) // 32 * 32
+        b += s * ldp * (2.0 * f["p"] + f["moves"])
+    return b
+
+
 CD_SOURCES = ["paper_2203_15031_gb300/csrc/cd_device.cuh", "paper_2203_15031_gb300/csrc/batch.cu"]
-PROFILE = "profiles/batch_cd_lazy_kernel_er_p2000_n200_x10.md"
+PROFILE = "profiles/batch_cd_lazy_kernel_batch256.md"
 
 
-def sweep_model(s, p, sweeps, moves, nnz_b, ms, hbm):
-    """Bytes of the row-synchronous schedule with G in memory, per launch:
-    every column sweep reads its p entries of G, every coordinate change
-    reads and writes a column of G and reads a row of S, and B is written.
-    The lazy kernel keeps no G and moves far fewer bytes, so at the bench
-    sizes (S in L2) this fraction compares the work done with what a
-    bandwidth-bound G schedule would need; it is not a traffic figure."""
-    b = float(s) * p * (sweeps + 3.0 * moves) + 2.0 * s * nnz_b
-    a = b / (ms / 1e3) / 1e9
-    return {"bytes_per_launch": b, "achieved": a, "frac": a / hbm,
-            "terms": "s*p*(column sweeps) + 2*s*p*moves + s*p*moves + 2*s*nnz(B)",
-            "column_sweeps": sweeps}
+def workload_sha() -> str:
+    """sha256 of the batched workload's definition: the shapes and seeds of
+    the 256 fits and the generator source."""
+    import hashlib
+    import synth
+    h = hashlib.sha256(json.dumps(synth.batch_specs(N_FITS)).encode())
+    with open(os.path.join(ROOT, "synth", "__init__.py")) as f:
+        h.update(f.read().encode())
+    return h.hexdigest()
 
 
 def measured_traffic():
-    """DRAM bytes per launch of the batched CD kernel from the committed ncu
-    summary, or None when the kernel source changed since that capture."""
+    """DRAM bytes per launch of the batched lazy kernel from the committed ncu
+    summary, or None when the kernel source or the workload changed since."""
     try:
         text = open(os.path.join(ROOT, PROFILE)).read()
     except OSError:
@@ -246,11 +286,14 @@ def measured_traffic():
     try:
         if vals.get("kernel_source_sha256", "").strip() != _sha_of(CD_SOURCES):
             return None
+        if vals.get("workload_sha256", "").strip() != workload_sha():
+            return None
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
 
 
+# ----------------------------------------------------------------------------- headline
 def run_ours(args):
     import numpy as np
     import torch
@@ -265,117 +308,88 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     sp.lib()
 
-    w, probs = make_inputs(N_DATASETS)
-    p, n, tol, maxit = w["p"], w["n"], w["tol"], w["maxit"]
+    probs = batch_problems()
     inputs = [(torch.from_numpy(pr.X).to(dev), pr.lambda0) for pr in probs]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
-    # ---- batched paths: one batch = the ten datasets
-    def batched(prec, sampler=None):
-        bt = sp.Batch(inputs, kind="X", precision=prec, tol=tol, maxit=maxit,
-                      record_phase_times=True)
-        bt.run()
-        bt.result()
-        best_w = bt.tune()
-        for _ in range(args.warmup):
-            bt.run()
-        statuses, _ = bt.result()
-        if any(s != sp.SPMESL_OK for s in statuses):
-            raise RuntimeError(f"warm-up fits did not converge: {statuses}")
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        cd_ms, moves, sweeps, nnzb, act = [], [], [], [], []
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if sampler:
-            sampler.__enter__()
+    # ---- batched mixed path (headline): one graph replay per step
+    bt = sp.Batch(inputs, kind="X", precision=BATCH_PREC, tol=TOL, maxit=MAXIT, use_graph=True)
+    best_w = bt.tune()
+    for _ in range(args.warmup):
+        bt.run(stream)
+    statuses, _ = bt.result(stream)
+    if any(s not in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED) for s in statuses):
+        raise RuntimeError(f"warm-up batch failed: {statuses}")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank)
+    with clk:
         for i in range(args.steps):
             flush.zero_()                   # evict the inputs from L2 between steps
             ev[i][0].record(stream)
             bt.run(stream)
             ev[i][1].record(stream)
-            statuses, st = bt.result(stream)
-            cd_ms.append(st["ms_cd"])
-            moves.append(st["moves"])
-            sweeps.append(st["inner_sweeps"])
-            nnzb.append(st["nnz_B"])
-            act.append((st["active_sweeps"], st["active_moves"]))
         torch.cuda.synchronize()
-        if sampler:
-            sampler.__exit__(None, None, None)
-        if world > 1:
-            dist.barrier()
-        per = [a.elapsed_time(b) for a, b in ev]
-        total_ms = max_over_ranks(sum(per), dev)
-        return bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb, act
+    if world > 1:
+        dist.barrier()
+    per = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(per), dev)
+    value = whole_job_rate(N_FITS * args.steps, world, total_ms)
+    statuses, agg = bt.result(stream)
 
-    clk = ClockSampler(local_rank)
-    bt, best_w, per, total_ms, cd_ms, moves, sweeps, nnzb, act = batched(BATCH_PREC, clk)
-    value = whole_job_rate(N_DATASETS * args.steps, world, total_ms)
-    bt32, _, per32, total32, _, _, _, _, _ = batched("fp32")
-    value32 = whole_job_rate(N_DATASETS * args.steps, world, total32)
-    bt32.close()
-
-    # ---- plain path: one fit per launch sequence, serialised on one stream
-    S = torch.empty((p, p), dtype=torch.float32, device=dev)
-    Theta = torch.empty((p, p), dtype=torch.float64, device=dev)
-    sigma = torch.empty(p, dtype=torch.float64, device=dev)
-    gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
-    fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
-    gkeep, gws = sp._workspace(gnb, dev)
-    fkeep, fws = sp._workspace(fnb, dev)
-    opts = sp.spmesl_default_opts()
-    opts.precision = sp.FP32
-
-    def plain_fit(i):
-        X, lam = inputs[i % N_DATASETS]
-        sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S, p, gws, gnb, stream), "spmesl_gram")
-        sp._check(sp.spmesl_fit(S, n, p, lam, tol, maxit, opts, Theta, sigma, None, fws, fnb,
-                                stream), "spmesl_fit")
-
-    for i in range(args.warmup):
-        plain_fit(i)
-    torch.cuda.synchronize()
-    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps * N_DATASETS)]
-    for s in range(args.steps):
+    # ---- the coordinate-descent launches of a step: CUDA events around them
+    # in a replay without the graph (same fits), with the distinct moved
+    # coordinates counted on the device
+    btc = sp.Batch(inputs, kind="X", precision=BATCH_PREC, tol=TOL, maxit=MAXIT,
+                   warps_per_block=best_w, record_phase_times=True, count_rows=True)
+    cd_ms = []
+    for i in range(args.warmup + args.steps):
         flush.zero_()
-        for d in range(N_DATASETS):
-            e0, e1 = pev[s * N_DATASETS + d]
-            e0.record(stream)
-            plain_fit(d)
-            e1.record(stream)
-    torch.cuda.synchronize()
-    plain_per = [a.elapsed_time(b) for a, b in pev]
-    plain_value = len(plain_per) / (sum(plain_per) / 1e3)
-    plain_fit(0)                            # dataset 0 against the batched result
-    torch.cuda.synchronize()
-    dtheta_plain = float((bt.Theta[0] - Theta).abs().max() / Theta.abs().max())
+        btc.run(stream)
+        _, stc = btc.result(stream)
+        if i >= args.warmup:
+            cd_ms.append(stc["ms_cd"])
+    fit_counters = []
+    for i, pr in enumerate(probs):
+        fs = btc.fit_stats(i)
+        fit_counters.append(dict(p=pr.p, inner_sweeps=fs["inner_sweeps"], moves=fs["moves"],
+                                 rows_moved=fs["rows_moved"], nnz_B=fs["nnz_B"]))
+    if not torch.equal(btc.Theta[0], bt.Theta[0]):
+        raise RuntimeError("counting changed the result")
+    btc.close()
 
-    # ---- end to end through the public API with host buffers (pinned): every
-    # step copies its ten X in and its ten Theta and sigma out.  Two batches
-    # on two streams take the steps in turn, so the copies of one step run
-    # under the compute of the next (as a serving loop would).
+    # ---- diagnostics of every fit (one more run, outside the timed region)
+    btd = sp.Batch(inputs, kind="X", precision=BATCH_PREC, tol=TOL, maxit=MAXIT,
+                   warps_per_block=best_w, diagnostics=True)
+    btd.run(stream)
+    _, diag = btd.result(stream)
+    btd.close()
+
+    # ---- end to end through the C ABI with host buffers (pinned): every step
+    # copies its 256 X in and its 256 Theta and sigma out; two batches on two
+    # streams take the steps in turn, so one step's copies run under the next
+    # step's compute
     Xh = [torch.from_numpy(pr.X).pin_memory() for pr in probs]
     bt2 = sp.Batch([(X.clone(), lam) for X, lam in inputs], kind="X", precision=BATCH_PREC,
-                   tol=tol, maxit=maxit, warps_per_block=best_w)
+                   tol=TOL, maxit=MAXIT, use_graph=True, warps_per_block=best_w)
     slots = [bt, bt2]
     streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
-    Th = [[torch.empty((p, p), dtype=torch.float64).pin_memory() for _ in range(N_DATASETS)]
+    Th = [[torch.empty((pr.p, pr.p), dtype=torch.float64).pin_memory() for pr in probs]
           for _ in range(2)]
-    sh = [[torch.empty(p, dtype=torch.float64).pin_memory() for _ in range(N_DATASETS)]
-          for _ in range(2)]
+    sh = [[torch.empty(pr.p, dtype=torch.float64).pin_memory() for pr in probs] for _ in range(2)]
 
     def e2e_step(i):
         k = i % 2
         b, s = slots[k], streams[k]
         with torch.cuda.stream(s):
-            for d in range(N_DATASETS):
+            for d in range(N_FITS):
                 b.inputs[d].copy_(Xh[d], non_blocking=True)
             b.run(s)
-            for d in range(N_DATASETS):
+            for d in range(N_FITS):
                 Th[k][d].copy_(b.Theta[d], non_blocking=True)
                 sh[k][d].copy_(b.sigma[d], non_blocking=True)
 
@@ -389,20 +403,18 @@ def run_ours(args):
         e2e_step(i)
     for s in streams:
         s.synchronize()
-    e2e_s = time.perf_counter() - t0
-    bt2.close()
-    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     if world > 1:
         dist.barrier()
-    e2e = {"value": whole_job_rate(N_DATASETS * args.steps, world, e2e_s * 1e3),
-           "unit": "solves/s",
-           "h2d_bytes_per_step": N_DATASETS * n * p * 4,
-           "d2h_bytes_per_step": N_DATASETS * (p * p * 8 + p * 8),
+    h2d = sum(pr.n * pr.p * 4 for pr in probs)
+    d2h = sum(pr.p * pr.p * 8 + pr.p * 8 for pr in probs)
+    e2e = {"value": whole_job_rate(N_FITS * args.steps, world, e2e_s * 1e3), "unit": "solves/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "pipeline": "two batches on two streams in turn; host waits at the end"}
-    # The bound of the end-to-end number: the device-to-host link, measured as
-    # one more copy of a step's Theta bytes into pinned host memory (best of 3)
-    lk_src = torch.zeros(N_DATASETS * p * p, dtype=torch.float64, device=dev)
-    lk_dst = torch.empty(N_DATASETS * p * p, dtype=torch.float64).pin_memory()
+    # the link that bounds it: one more copy of a step's Theta bytes into
+    # pinned host memory (best of 3)
+    lk_src = torch.zeros(d2h // 8, dtype=torch.float64, device=dev)
+    lk_dst = torch.empty(d2h // 8, dtype=torch.float64).pin_memory()
     lk = []
     for _ in range(3):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -411,74 +423,337 @@ def run_ours(args):
         b.record(stream)
         b.synchronize()
         lk.append(a.elapsed_time(b))
-    link_gbs = lk_src.numel() * 8 / (min(lk) / 1e3) / 1e9
-    ceiling = world * N_DATASETS * link_gbs * 1e9 / e2e["d2h_bytes_per_step"]
+    link_gbs = d2h / (min(lk) / 1e3) / 1e9
     e2e["link_d2h_gbs"] = link_gbs
-    e2e["link_ceiling_solves_per_s"] = ceiling
-    e2e["frac_of_link_ceiling"] = e2e["value"] / ceiling
-    del lk_src, lk_dst
+    e2e["link_ceiling_solves_per_s"] = world * N_FITS * link_gbs * 1e9 / d2h
+    e2e["frac_of_link_ceiling"] = e2e["value"] / e2e["link_ceiling_solves_per_s"]
+    del lk_src, lk_dst, Th, sh, Xh
+    bt2.close()
 
-    if rank == 0:
-        hbm, which = _peaks()
-        # algorithmic bytes of one batched CD launch: every column reads S_.j
-        # and writes b_j (2 p rows of ldp floats per fit), and every move of a
-        # full sweep reads one S row (the column slice of the rank-1 update);
-        # moves of the active-set phase read the support's block of S, held
-        # in shared memory, and are counted apart
-        ldp = (p + 31) // 32 * 32
-        mv = statistics.mean(moves)
-        bytes_cd = 4.0 * ldp * (2 * p * N_DATASETS + mv)
-        cd_mean_ms = statistics.mean(cd_ms)
-        achieved = bytes_cd / (cd_mean_ms / 1e3) / 1e9
-        traffic = measured_traffic()
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic,
-                "kernel": "batch_cd_lazy_kernel<float,1>", "peak_kind": which,
-                "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cd_mean_ms,
-                "moves_per_launch": mv, "warps_per_block": best_w,
-                "active_sweeps_per_launch": statistics.mean(a for a, _ in act),
-                "active_moves_per_launch": statistics.mean(m for _, m in act),
-                "sweep_model": sweep_model(4, p, statistics.mean(sweeps), mv,
-                                           statistics.mean(nnzb), cd_mean_ms, hbm)}
-        srt = sorted(per)
-        psrt = sorted(plain_per)
-        q99 = lambda v: v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)]
-        lat = {"batched_p50_ms": statistics.median(per), "batched_p99_ms": q99(srt),
-               "plain_p50_ms": statistics.median(plain_per), "plain_p99_ms": q99(psrt),
-               "unit": "ms from launch to completion of a solve (device)"}
-        cb = (cpu_baseline(w, probs[0], theta_gpu=bt.Theta[0].cpu().numpy())
-              if world == 1 and not args.no_cpu_baseline else None)
-        acc = {"max_rel_dtheta_vs_plain_fp32": dtheta_plain, "dataset": "seed 0",
-               "bound": 1e-4}
-        if cb is not None:
-            acc["max_rel_dtheta_vs_fp64_oracle"] = cb.pop("gpu_max_rel_dtheta")
-        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "p": p, "n": n, "network": "erdos_renyi",
-                           "fits_per_step": N_DATASETS, "seeds": "0-9",
-                           "lambda0": "sqrt(2 log p / n)", "tol": tol, "maxit": maxit,
-                           "precision": BATCH_PREC,
-                           "gram": "split-bf16 on tcgen05 (hi*hi + hi*lo + lo*hi, fp32 accumulation)",
-                           "cd": "fp32", "sigma_theta": "fp64",
-                           "inner_rule": "column", "path": "batched (one launch per phase)",
-                           "l2": "flushed between steps (256 MB write)",
-                           "parallelism": f"replicas x{world}"},
-                "plain": {"value": plain_value, "unit": "solves/s", "precision": "fp32",
-                          "path": "one spmesl_gram + spmesl_fit per fit, serialised"},
-                "batched_fp32": {"value": value32, "unit": "solves/s",
-                                 "p50_ms": statistics.median(per32),
-                                 "path": "the same batch with the FP32 SIMT Gram"},
-                "accuracy": acc,
-                "latency": lat, "e2e": e2e, "roofline": roof, "cpu_baseline": cb,
-                "gpu_launches": KERNELS_PER_SOLVE[BATCH_PREC] * args.steps,
-                "clocks": clk.summary()}
-        print(json.dumps(line), flush=True)
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- plain path over the same fits: one spmesl_gram + spmesl_fit per fit
+    # through the C ABI, buffers allocated beforehand, serialised on the
+    # stream (the second of two passes timed, one event pair per fit)
+    opts = sp.spmesl_default_opts()
+    opts.precision = sp.FP32
+    bufs = []
+    for (X, lam), pr in zip(inputs, probs):
+        p, n = pr.p, pr.n
+        gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
+        fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
+        bufs.append((X, lam, p, n, torch.empty((p, p), dtype=torch.float32, device=dev),
+                     torch.empty((p, p), dtype=torch.float64, device=dev),
+                     torch.empty(p, dtype=torch.float64, device=dev),
+                     sp._workspace(max(gnb, 1), dev), gnb, sp._workspace(fnb, dev), fnb))
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in bufs]
+    for rep in range(2):
+        flush.zero_()
+        for (X, lam, p, n, S, T, sg, (gk, gws), gnb, (fk, fws), fnb), (e0, e1) in zip(bufs, pev):
+            e0.record(stream)
+            sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S, p, gws, gnb, stream), "gram")
+            sp._check(sp.spmesl_fit(S, n, p, lam, TOL, MAXIT, opts, T, sg, None, fws, fnb,
+                                    stream), "fit")
+            e1.record(stream)
+        torch.cuda.synchronize()
+    plain_per = [a.elapsed_time(b) for a, b in pev]
+    plain_value = len(plain_per) / (sum(plain_per) / 1e3)
+    plain_theta = {i: bufs[i][5].cpu().numpy() for i in ORACLE_SAMPLE}
+    del bufs
+
+    # ---- the served workload (continuous batching) against the plain path
+    served = serve_block(dev, requests=args.serve_requests, pool=args.serve_pool,
+                         fracs=args.serve_fracs, sat_reps=3)
+
+    # ---- the single-shape batch: ten ER p=2000 n=200 fits
+    er10 = er10_block(dev, args.steps, args.warmup)
+
+    # ---- accuracy and the CPU baseline: the FP64 oracle on the step's fits
+    hbm, which = _peaks()
+    acc = {"bound": 1e-4, "sample": "all 256 fits of the step"}
+    cb = None
+    if not args.no_cpu_baseline:
+        cb, ref = cpu_baseline(probs)
+        acc["max_rel_dtheta_batched_mixed_vs_fp64_oracle"] = max(
+            rel_err(bt.Theta[i].cpu().numpy(), ref[i]) for i in ref)
+        acc["max_rel_dtheta_plain_fp32_vs_fp64_oracle"] = max(
+            rel_err(plain_theta[i], ref[i]) for i in ref)
+    acc["device_diagnostics"] = {"err_est_max": diag["err_est"], "kkt_viol_max": diag["kkt_viol"],
+                                 "dual_gap_max": diag["dual_gap"],
+                                 "of": "all 256 fits (err_est: estimate of max|dTheta|/max|Theta|)"}
+
+    # ---- roofline of the coordinate-descent launches
+    cdm = statistics.mean(cd_ms)
+    bytes_gs = gschedule_bytes(4, fit_counters)
+    bytes_col = column_bytes(4, fit_counters)
+    achieved = bytes_gs / (cdm / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": measured_traffic(),
+            "kernel": "batch_cd_lazy_kernel<float,1> + batch_cd_block_kernel<float,1> "
+                      "(the coordinate-descent launches of a step)",
+            "peak_kind": which, "model": "row-synchronous schedule with G in memory: "
+            "s*p*(column sweeps) + 2*s*p*moves + s*p*(distinct rows moved per sweep index) "
+            "+ 2*s*nnz(B), s = 4, counted on the device per fit",
+            "algorithmic_bytes_per_launch": bytes_gs, "mean_launch_ms": cdm,
+            "cd_timing": "CUDA events around the coordinate-descent launches on the batch's "
+                         "stream, in a replay without the graph (same fits, L2 flushed)",
+            "column_sweeps": sum(f["inner_sweeps"] for f in fit_counters),
+            "moves": sum(f["moves"] for f in fit_counters),
+            "rows_moved": sum(f["rows_moved"] for f in fit_counters),
+            "per_column_model": {"bytes_per_launch": bytes_col,
+                                 "achieved": bytes_col / (cdm / 1e3) / 1e9,
+                                 "frac": bytes_col / (cdm / 1e3) / 1e9 / hbm},
+            "warps_per_block": best_w, "block_columns": agg["block_columns"],
+            "note": "S of most fits sits in L2: the model's bytes are work-equivalent, "
+                    "the traffic key gives the DRAM bytes ncu counted"}
+    srt = sorted(per)
+    psrt = sorted(plain_per)
+    q = lambda v, f: v[min(len(v) - 1, int(math.ceil(f * len(v))) - 1)]
+    lat = {"batched_p50_ms": statistics.median(per), "batched_p99_ms": q(srt, 0.99),
+           "plain_p50_ms": statistics.median(plain_per), "plain_p99_ms": q(psrt, 0.99),
+           "unit": "ms from launch to completion of a solve (device); a batched solve "
+                   "completes with its step"}
+    ps = [pr.p for pr in probs]
+    ns = [pr.n for pr in probs]
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "fits_per_step": N_FITS,
+                       "p": f"log-uniform [50, 2000] (drawn {min(ps)}-{max(ps)})",
+                       "n": f"uniform [30, 400] (drawn {min(ns)}-{max(ns)})",
+                       "networks": "ar1 / er / hub_scaled at random", "seeds": "1000-1255",
+                       "lambda0": "sqrt(2 log p / n)", "tol": TOL, "maxit": MAXIT,
+                       "precision": BATCH_PREC,
+                       "gram": "split-bf16 on tcgen05 (hi*hi + hi*lo + lo*hi, fp32 accumulation)",
+                       "cd": "fp32", "sigma_theta": "fp64", "graph": True,
+                       "warps_per_block": best_w, "inner_rule": "column",
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "plain": {"value": plain_value, "unit": "solves/s", "precision": "fp32",
+                      "path": "one spmesl_gram + spmesl_fit per fit, serialised"},
+            "latency": lat, "served": served, "er_p2000_x10": er10, "accuracy": acc,
+            "e2e": e2e, "roofline": roof, "cpu_baseline": cb,
+            "statuses": {"ok": sum(s == sp.SPMESL_OK for s in statuses), "of": N_FITS},
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
     bt.close()
-    del gkeep, fkeep
     if world > 1:
+        dist.barrier()
         dist.destroy_process_group()
+
+
+def serve_pool(dev, pool: int):
+    """The serving workload's datasets: p log-uniform in [100, 5000],
+    n = max(p/4, 50), networks in turn, request i of the pool seed 2000 + i."""
+    import numpy as np
+    import torch
+    import synth
+    rng = np.random.default_rng(7)
+    kinds = ["ar1", "er", "hub_scaled"]
+    out = []
+    for i in range(pool):
+        p = int(round(math.exp(rng.uniform(math.log(100), math.log(5000)))))
+        n = max(p // 4, 50)
+        pr = synth.make_problem(kinds[i % 3], p, n, 2000 + i, dtype=np.float32)
+        out.append((torch.from_numpy(pr.X).to(dev), pr.lambda0, p, n))
+    return out, rng
+
+
+def serve_block(dev, requests: int = 200, pool: int = 24, fracs=(0.5, 0.9), sat_reps: int = 3):
+    """Served path (spmesl_ctx: continuous batching under a 120 GB budget,
+    mixed precision) against the plain path (one FP32 fit per launch,
+    first-come first-served on one stream), fed the same Poisson arrivals at
+    fractions of the served saturation rate.  Latency = completion - arrival
+    per request (host clock).  Saturation: every request submitted at once,
+    repeated sat_reps times."""
+    import numpy as np
+    import torch
+
+    import paper_2203_15031_gb300 as sp
+
+    data, rng = serve_pool(dev, pool)
+    R = requests
+    order = rng.integers(0, len(data), R)
+
+    def serve_run(rate):
+        srv = sp.Server(120 << 30, max_slots=256, precision=BATCH_PREC, tol=TOL, maxit=MAXIT)
+        gaps = rng.exponential(1.0 / rate, R) if rate else np.zeros(R)
+        arrivals = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        live, lat, done_t = {}, [], []
+        k = 0
+        while k < R or live:
+            now = time.perf_counter() - t0
+            while k < R and arrivals[k] <= now:
+                X, lam, _, _ = data[order[k]]
+                live[srv.submit(X, lam)] = k
+                k += 1
+            for t in list(live):
+                r = srv.poll(t)
+                if r is not None:
+                    if r[0] not in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED):
+                        raise RuntimeError(f"request failed: {r[0]}")
+                    lat.append(r[3]["ms_total"])
+                    done_t.append(time.perf_counter() - t0)
+                    del live[t]
+            if not live and k < R:
+                time.sleep(max(0.0, min(0.001, arrivals[k] - (time.perf_counter() - t0))))
+        srv.close()
+        return R / (max(done_t) - arrivals[0]), lat
+
+    S, ws = {}, {}
+    opts = sp.spmesl_default_opts()
+    opts.precision = sp.FP32
+
+    def plain_fit(idx):
+        X, lam, p, n = data[idx]
+        if p not in S:
+            S[p] = torch.empty((p, p), dtype=torch.float32, device=dev)
+            gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
+            fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
+            ws[p] = (sp._workspace(max(gnb, 1), dev), gnb, sp._workspace(fnb, dev), fnb,
+                     torch.empty((p, p), dtype=torch.float64, device=dev),
+                     torch.empty(p, dtype=torch.float64, device=dev))
+        (gk, gws), gnb, (fk, fws), fnb, Th, sg = ws[p]
+        sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S[p], p, gws, gnb), "spmesl_gram")
+        sp._check(sp.spmesl_fit(S[p], n, p, lam, TOL, MAXIT, opts, Th, sg, None, fws, fnb),
+                  "spmesl_fit")
+        torch.cuda.current_stream().synchronize()
+
+    def plain_run(rate):
+        gaps = rng.exponential(1.0 / rate, R) if rate else np.zeros(R)
+        arrivals = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        lat, done_t = [], []
+        for k in range(R):
+            now = time.perf_counter() - t0
+            if arrivals[k] > now:
+                time.sleep(arrivals[k] - now)
+            plain_fit(order[k])
+            t = time.perf_counter() - t0
+            lat.append(1e3 * (t - arrivals[k]))
+            done_t.append(t)
+        return R / (max(done_t) - arrivals[0]), lat
+
+    def q(v, f):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(math.ceil(f * len(v))) - 1)]
+
+    for i in range(len(data)):                # warm both paths (kernels, pools)
+        plain_fit(i)
+    serve_run(0)
+    sats = [serve_run(0)[0] for _ in range(sat_reps)]
+    sat_serve = statistics.median(sats)
+    sat_plain, _ = plain_run(0)
+    rows = []
+    for frac in fracs:
+        rate = frac * sat_serve
+        sv, slat = serve_run(rate)
+        pv, plat = plain_run(rate)
+        rows.append({"arrival_rate": rate, "fraction_of_saturation": frac,
+                     "served": {"solves_per_s": sv, "p50_ms": q(slat, 0.5), "p99_ms": q(slat, 0.99)},
+                     "plain": {"solves_per_s": pv, "p50_ms": q(plat, 0.5), "p99_ms": q(plat, 0.99)}})
+    return {"config": {"requests": R, "datasets": len(data), "p": "log-uniform [100, 5000]",
+                       "n": "max(p/4, 50)", "networks": "ar1 / er / hub_scaled",
+                       "budget_gb": 120, "max_slots": 256, "precision": BATCH_PREC,
+                       "plain_precision": "fp32", "arrivals": "Poisson, seed 7"},
+            "saturation": {"served_solves_per_s": sat_serve, "served_runs": sats,
+                           "served_spread": [min(sats), max(sats)],
+                           "plain_solves_per_s": sat_plain},
+            "rates": rows, "unit": "solves/s; latency ms from arrival to completion (host)"}
+
+
+def er10_block(dev, steps: int, warmup: int):
+    """Ten ER p=2000 n=200 fits (seeds 0-9) as one mixed batch, one graph
+    replay per step, L2 flushed between steps."""
+    import numpy as np
+    import torch
+
+    import paper_2203_15031_gb300 as sp
+    import synth
+    probs = [synth.make_problem("er", 2000, 200, s, dtype=np.float32) for s in range(10)]
+    inputs = [(torch.from_numpy(pr.X).to(dev), pr.lambda0) for pr in probs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    bt = sp.Batch(inputs, kind="X", precision=BATCH_PREC, tol=TOL, maxit=MAXIT, use_graph=True)
+    w = bt.tune()
+    for _ in range(warmup):
+        bt.run(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        bt.run(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    bt.close()
+    return {"value": 10 * steps / (sum(per) / 1e3), "unit": "solves/s",
+            "ms_per_step": statistics.mean(per), "p": 2000, "n": 200, "network": "erdos_renyi",
+            "fits_per_step": 10, "seeds": "0-9", "precision": BATCH_PREC, "warps_per_block": w}
+
+
+def run_er10(args):
+    import torch
+    import paper_2203_15031_gb300 as sp
+    torch.cuda.set_device(0)
+    sp.lib()
+    out = er10_block(torch.device("cuda", 0), args.steps, args.warmup)
+    print(json.dumps({"metric": METRIC, "workload": "er_p2000_n200_x10", **out}), flush=True)
+
+
+def run_serve(args):
+    import torch
+    import paper_2203_15031_gb300 as sp
+    torch.cuda.set_device(0)
+    sp.lib()
+    out = serve_block(torch.device("cuda", 0), requests=args.serve_requests, pool=args.serve_pool,
+                      fracs=args.serve_fracs, sat_reps=3)
+    print(json.dumps({"metric": METRIC, "workload": "serve", **out}), flush=True)
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores: each step solves a
+    bounded sample of the batched workload (every 32nd fit: Gram, then
+    Algorithm 2 with OpenMP over columns on all cores)."""
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return
+    probs = batch_problems(REFERENCE_SAMPLE)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(probs, REFERENCE_SAMPLE[:1], cores)
+    times = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_sample(probs, REFERENCE_SAMPLE, cores)
+        times.append(time.perf_counter() - t0)
+    total = time.perf_counter() - t_all
+    value = len(REFERENCE_SAMPLE) * args.steps / total
+    ps = [probs[i].p for i in REFERENCE_SAMPLE]
+    sample = (f"{len(REFERENCE_SAMPLE)} of the 256 fits per step (every 32nd, p {min(ps)}-"
+              f"{max(ps)}): FP64 Gram + Algorithm 2, OpenMP over columns on all cores")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "fits_per_step": len(REFERENCE_SAMPLE),
+                       "p": "log-uniform [50, 2000]", "n": "uniform [30, 400]",
+                       "networks": "ar1 / er / hub_scaled at random", "seeds": "1000-1255",
+                       "lambda0": "sqrt(2 log p / n)", "tol": TOL, "maxit": MAXIT},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def run_single(args):
@@ -514,6 +789,7 @@ def run_single(args):
     opts = sp.spmesl_default_opts()
     opts.precision = prec
     opts.record_phase_times = 1
+    opts.count_rows = 1
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -531,7 +807,7 @@ def run_single(args):
     st = sp.Stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    gram_ms, cd_ms, moves, sweeps, nnzb, act_s, act_m = [], [], [], [], [], [], []
+    gram_ms, cd_ms, moves, sweeps, nnzb, act_s, act_m, rows = [], [], [], [], [], [], [], []
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         for i in range(args.steps):
@@ -547,23 +823,32 @@ def run_single(args):
             nnzb.append(st.nnz_B)
             act_s.append(st.active_sweeps)
             act_m.append(st.active_moves)
+            rows.append(st.rows_moved)
         torch.cuda.synchronize()
     per = [a.elapsed_time(b) for a, b in ev]
     value = args.steps / (sum(per) / 1e3)
     hbm, which = _peaks()
-    ldp = (p + 31) // 32 * 32
     s = 8 if prec == sp.FP64 else 4
-    mv = statistics.mean(moves)
-    bytes_cd = float(s) * ldp * (2 * p + mv)
+    counters = [dict(p=p, inner_sweeps=statistics.mean(sweeps), moves=statistics.mean(moves),
+                     rows_moved=statistics.mean(rows), nnz_B=statistics.mean(nnzb))]
+    bytes_gs = gschedule_bytes(s, counters)
+    bytes_col = column_bytes(s, counters)
     cdm = statistics.mean(cd_ms)
-    roof = {"bound": "hbm", "achieved": bytes_cd / (cdm / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": bytes_cd / (cdm / 1e3) / 1e9 / hbm, "traffic": None,
-            "kernel": "cd_column_lazy_kernel", "peak_kind": which,
-            "algorithmic_bytes_per_launch": bytes_cd, "mean_launch_ms": cdm, "moves_per_launch": mv,
+    roof = {"bound": "hbm", "achieved": bytes_gs / (cdm / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": bytes_gs / (cdm / 1e3) / 1e9 / hbm, "traffic": None,
+            "kernel": "cd_column_lazy_kernel + cd_column_block_kernel (the coordinate-descent "
+                      "launches of the fit)", "peak_kind": which,
+            "model": "row-synchronous schedule with G in memory (device-counted sweeps, moves, "
+                     "distinct rows moved per sweep index)",
+            "algorithmic_bytes_per_launch": bytes_gs, "mean_launch_ms": cdm,
+            "column_sweeps": counters[0]["inner_sweeps"], "moves": counters[0]["moves"],
+            "rows_moved": counters[0]["rows_moved"],
             "active_sweeps_per_launch": statistics.mean(act_s),
             "active_moves_per_launch": statistics.mean(act_m),
-            "sweep_model": sweep_model(s, p, statistics.mean(sweeps), mv, statistics.mean(nnzb),
-                                       cdm, hbm)}
+            "block_columns": st.block_columns,
+            "per_column_model": {"bytes_per_launch": bytes_col,
+                                 "achieved": bytes_col / (cdm / 1e3) / 1e9,
+                                 "frac": bytes_col / (cdm / 1e3) / 1e9 / hbm}}
     gm = statistics.mean(gram_ms)
     roof_gram = None
     if prec == sp.MIXED:
@@ -593,7 +878,11 @@ def run_single(args):
             "latency": {"p50_ms": statistics.median(per),
                         "p99_ms": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]},
             "roofline": roof, "roofline_gram": roof_gram,
-            "gpu_launches": ((2 if prec == sp.MIXED else 1) + 5) * args.steps,
+            # Gram (split + tcgen05, or SIMT); prep_diag, prep_matrix, [column
+            # order], [block solver on the heavy columns], lazy, block solver on
+            # the handed-over columns, row count, Theta zeroing, Theta
+            "gpu_launches": ((2 if prec == sp.MIXED else 1) + 7 + (1 if p >= 4096 else 0)
+                             + (1 if p >= 3648 else 0)) * args.steps,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     del gkeep, fkeep
@@ -702,209 +991,6 @@ def run_residual(args):
             # Theta zeroing and Theta per residual fit
             "gpu_launches": 5 * args.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
-
-
-def run_serve(args):
-    """Serving workload: Poisson arrivals of requests with p log-uniform in
-    [100, 5000], n = max(p/4, 50), networks mixed; continuous batching
-    (spmesl_ctx, 120 GB admission budget) against the plain path (one fit per
-    launch, first-come first-served on one stream), at arrival rates that
-    are fractions of the measured saturation throughput."""
-    import numpy as np
-    import torch
-
-    import paper_2203_15031_gb300 as sp
-    import synth
-
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    sp.lib()
-    rng = np.random.default_rng(7)
-    kinds = ["ar1", "er", "hub_scaled"]
-    pool = []
-    for i in range(args.serve_pool):
-        p = int(round(math.exp(rng.uniform(math.log(100), math.log(5000)))))
-        n = max(p // 4, 50)
-        pr = synth.make_problem(kinds[i % 3], p, n, 2000 + i, dtype=np.float32)
-        pool.append((torch.from_numpy(pr.X).to(dev), pr.lambda0, p, n))
-    R = args.serve_requests
-    order = rng.integers(0, len(pool), R)
-    tol, maxit = 1e-6, 1000
-
-    def serve_run(rate):
-        srv = sp.Server(120 << 30, max_slots=256, precision=BATCH_PREC, tol=tol, maxit=maxit)
-        gaps = rng.exponential(1.0 / rate, R) if rate else np.zeros(R)
-        arrivals = np.cumsum(gaps)
-        t0 = time.perf_counter()
-        live, lat, done_t = {}, [], []
-        k = 0
-        while k < R or live:
-            now = time.perf_counter() - t0
-            while k < R and arrivals[k] <= now:
-                X, lam, _, _ = pool[order[k]]
-                live[srv.submit(X, lam)] = k
-                k += 1
-            for t in list(live):
-                r = srv.poll(t)
-                if r is not None:
-                    if r[0] not in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED):
-                        raise RuntimeError(f"request failed: {r[0]}")
-                    lat.append(r[3]["ms_total"])
-                    done_t.append(time.perf_counter() - t0)
-                    del live[t]
-            if not live and k < R:
-                time.sleep(max(0.0, min(0.001, arrivals[k] - (time.perf_counter() - t0))))
-        srv.close()
-        span = max(done_t) - arrivals[0]
-        return R / span, lat
-
-    S = {}
-    ws = {}
-
-    def plain_fit(idx):
-        X, lam, p, n = pool[idx]
-        if p not in S:
-            S[p] = torch.empty((p, p), dtype=torch.float32, device=dev)
-            gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
-            fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
-            ws[p] = (sp._workspace(max(gnb, 1), dev), gnb, sp._workspace(fnb, dev), fnb,
-                     torch.empty((p, p), dtype=torch.float64, device=dev),
-                     torch.empty(p, dtype=torch.float64, device=dev))
-        (gk, gws), gnb, (fk, fws), fnb, Th, sg = ws[p]
-        opts = sp.spmesl_default_opts()
-        opts.precision = sp.FP32
-        sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S[p], p, gws, gnb), "spmesl_gram")
-        sp._check(sp.spmesl_fit(S[p], n, p, lam, tol, maxit, opts, Th, sg, None, fws, fnb),
-                  "spmesl_fit")
-        torch.cuda.current_stream().synchronize()
-
-    def plain_run(rate):
-        gaps = rng.exponential(1.0 / rate, R) if rate else np.zeros(R)
-        arrivals = np.cumsum(gaps)
-        t0 = time.perf_counter()
-        lat, done_t = [], []
-        for k in range(R):
-            now = time.perf_counter() - t0
-            if arrivals[k] > now:
-                time.sleep(arrivals[k] - now)
-            plain_fit(order[k])
-            t = time.perf_counter() - t0
-            lat.append(1e3 * (t - arrivals[k]))
-            done_t.append(t)
-        return R / (max(done_t) - arrivals[0]), lat
-
-    def q(v, f):
-        v = sorted(v)
-        return v[min(len(v) - 1, int(math.ceil(f * len(v))) - 1)]
-
-    for i in range(len(pool)):                # warm both paths (kernels, pools)
-        plain_fit(i)
-    serve_run(0)
-    sat_serve, _ = serve_run(0)               # everything at once
-    sat_plain, _ = plain_run(0)
-    rows = []
-    for frac in args.serve_fracs:
-        rate = frac * sat_serve
-        sv, slat = serve_run(rate)
-        pv, plat = plain_run(rate)
-        rows.append({"arrival_rate": rate, "fraction_of_saturation": frac,
-                     "served": {"solves_per_s": sv, "p50_ms": q(slat, 0.5), "p99_ms": q(slat, 0.99)},
-                     "plain": {"solves_per_s": pv, "p50_ms": q(plat, 0.5), "p99_ms": q(plat, 0.99)}})
-    line = {"metric": METRIC, "workload": "serve",
-            "config": {"requests": R, "datasets": len(pool), "p": "log-uniform [100, 5000]",
-                       "n": "max(p/4, 50)", "networks": "ar1 / er / hub_scaled",
-                       "budget_gb": 120, "max_slots": 256, "precision": BATCH_PREC,
-                       "plain_precision": "fp32", "tol": tol,
-                       "arrivals": "Poisson, seed 7"},
-            "saturation": {"served_solves_per_s": sat_serve, "plain_solves_per_s": sat_plain},
-            "rates": rows, "unit": "solves/s; latency ms from arrival to completion"}
-    print(json.dumps(line), flush=True)
-
-
-def run_batch256(args):
-    """The 256-fit batch: p log-uniform in [50, 2000], n uniform in [30, 400],
-    networks AR(1) / Erdos-Renyi / hub at random (fit i: seed 1000 + i), one
-    CUDA-graph launch per step, mixed precision, warps per block autotuned;
-    against the plain path (one spmesl_gram + spmesl_fit per fit, FP32)."""
-    import numpy as np
-    import torch
-
-    import paper_2203_15031_gb300 as sp
-    import synth
-
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    sp.lib()
-    specs = synth.batch_specs(256)
-    probs = [synth.make_problem(s["kind"], s["p"], s["n"], s["seed"], dtype=np.float32)
-             for s in specs]
-    inputs = [(torch.from_numpy(pr.X).to(dev), pr.lambda0) for pr in probs]
-    tol, maxit = 1e-6, 1000
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    bt = sp.Batch(inputs, kind="X", precision=BATCH_PREC, tol=tol, maxit=maxit, use_graph=True)
-    w = bt.tune()
-    for _ in range(args.warmup):
-        bt.run(stream)
-    statuses, _ = bt.result(stream)
-    if any(s not in (sp.SPMESL_OK, sp.SPMESL_NOT_CONVERGED) for s in statuses):
-        raise RuntimeError(f"warm-up batch failed: {statuses}")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            bt.run(stream)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-    per = [a.elapsed_time(b) for a, b in ev]
-    value = 256 * args.steps / (sum(per) / 1e3)
-    _, st = bt.result(stream)
-    # plain path over the same fits: one spmesl_gram + spmesl_fit per fit
-    # through the C ABI, buffers allocated beforehand, serialised on the stream
-    # (two passes, the second timed)
-    opts = sp.spmesl_default_opts()
-    opts.precision = sp.FP32
-    bufs = []
-    for (X, lam), pr in zip(inputs, probs):
-        p, n = pr.p, pr.n
-        gnb = sp.spmesl_gram_workspace_bytes(n, p, sp.FP32)
-        fnb = sp.spmesl_fit_workspace_bytes(p, sp.FP32)
-        bufs.append((X, lam, p, n, torch.empty((p, p), dtype=torch.float32, device=dev),
-                     torch.empty((p, p), dtype=torch.float64, device=dev),
-                     torch.empty(p, dtype=torch.float64, device=dev),
-                     sp._workspace(max(gnb, 1), dev), gnb, sp._workspace(fnb, dev), fnb))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for rep in range(2):
-        e0.record(stream)
-        for X, lam, p, n, S, T, sg, (gk, gws), gnb, (fk, fws), fnb in bufs:
-            sp._check(sp.spmesl_gram(X, n, p, p, sp.FP32, 0, S, p, gws, gnb, stream), "gram")
-            sp._check(sp.spmesl_fit(S, n, p, lam, tol, maxit, opts, T, sg, None, fws, fnb,
-                                    stream), "fit")
-        e1.record(stream)
-        torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
-    del bufs
-    srt = sorted(per)
-    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sum(per) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch256", "fits_per_step": 256,
-                       "p": "log-uniform [50, 2000]", "n": "uniform [30, 400]",
-                       "networks": "ar1 / er / hub_scaled", "seeds": "1000-1255",
-                       "precision": BATCH_PREC, "graph": True, "warps_per_block": w,
-                       "tol": tol, "maxit": maxit, "l2": "flushed between steps (256 MB write)"},
-            "latency": {"p50_ms": statistics.median(per),
-                        "p99_ms": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]},
-            "plain": {"value": 256 / (plain_ms / 1e3), "unit": "solves/s", "precision": "fp32",
-                      "path": "one spmesl_gram + spmesl_fit per fit, serialised"},
-            "solve": {"moves": st["moves"], "full_sweeps": st["inner_sweeps"],
-                      "active_sweeps": st["active_sweeps"], "max_col_outer": st["max_col_outer"]},
-            "gpu_launches": KERNELS_PER_SOLVE[BATCH_PREC] * args.steps, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
-    bt.close()
 
 
 # Table 4 of the paper (values as printed, with their standard errors): the
@@ -1069,16 +1155,16 @@ def run_regression(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="default: the batched ER p=2000 line; other names in synth.WORKLOADS "
-                         "run single fits (measurement and profiling)")
+                    help="default: the 256-fit batch; er10, serve, regression, table4, residual, "
+                         "or a single-fit name of synth.WORKLOADS")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-pool", type=int, default=24)
-    ap.add_argument("--serve-fracs", type=float, nargs="+", default=[0.1, 0.5, 0.9, 1.1])
+    ap.add_argument("--serve-fracs", type=float, nargs="+", default=[0.5, 0.9])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -1086,10 +1172,10 @@ def main():
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "er10":
+        run_er10(args)
     elif args.workload == "regression":
         run_regression(args)
-    elif args.workload == "batch256":
-        run_batch256(args)
     elif args.workload == "table4":
         run_table4(args)
     elif args.workload == "residual":
