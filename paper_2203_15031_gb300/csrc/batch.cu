@@ -241,6 +241,8 @@ __global__ void __launch_bounds__(512) batch_cd_kernel(const BatchFit* __restric
     }
 }
 
+constexpr int PREFIX_SMEM = 1024;
+
 // Lazy gradient over all columns of all fits; overflowing columns are queued
 // for the block solver, and the first n_heavy columns of the heat order
 // belong to it from the start.
@@ -256,10 +258,17 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
                                                             const int* __restrict__ order,
                                                             int ovf_supp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the column prefix in shared memory: every column starts with a search of it
+    __shared__ int sprefix[PREFIX_SMEM];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)warp * lazy_warp_smem_bytes<T>(max_ldp);
     const int q0 = order ? *reinterpret_cast<volatile int*>(&hdr->n_heavy) : 0;
+    const bool sp = count < PREFIX_SMEM;
+    if (sp)
+        for (int i = threadIdx.x; i <= count; i += blockDim.x) sprefix[i] = col_prefix[i];
+    __syncthreads();
+    const int* __restrict__ prefix = sp ? sprefix : col_prefix;
     for (;;) {
         int gc = 0;
         if (lane == 0) {
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(32 * LAZY_MAX_WARPS, 3) batch_cd_lazy_kernel(c
         }
         gc = __shfl_sync(FULL_MASK, gc, 0);
         if (gc >= total_cols) break;
-        const int fi = find_fit(col_prefix, count, gc);
+        const int fi = find_fit(prefix, count, gc);
         const BatchFit& f = fits[fi];
         if (*reinterpret_cast<volatile int*>(&f.ctrl->err) != 0) continue;
         const CDArgs<T> a = column_args<T>(f, tol, maxit, ovf_supp);

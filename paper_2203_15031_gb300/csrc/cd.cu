@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(512) cd_column_kernel(CDArgs<T> a, int from_qu
 // Lazy gradient (sorted support in shared memory); columns whose support
 // outgrows the list go to the queue for cd_column_kernel.
 template <typename T, bool STD>
-__global__ void __launch_bounds__(512) cd_column_lazy_kernel(CDArgs<T> a) {
+__global__ void __launch_bounds__(256, 3) cd_column_lazy_kernel(CDArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -594,7 +594,7 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     auto lk = cd_column_lazy_kernel<T, STD>;
     const size_t lper = lazy_warp_smem_bytes<T>(L.ldp);
     int LW = f.warps_per_block > 0 ? f.warps_per_block : 8;
-    LW = std::max(1, std::min({LW, 16, (int)(smem_budget() / lper)}));
+    LW = std::max(1, std::min({LW, 8, (int)(smem_budget() / lper)}));
     const size_t lsm = lper * LW;
     int lper_sm = 1;
     if (lazy) {

@@ -547,16 +547,29 @@ __device__ __forceinline__ void flush_counters(FitCtrl* ctrl, ColCounters& c) {
 // test |F(sigma) - sigma| < tol and the returned pair (b(sigma), F(sigma)) are
 // Algorithm 1's, so the fit ends at the same fixed point within tol; about
 // 40 % fewer sigma steps reach it.  Any accepted step is a valid next sigma,
-// so the secant slope is formed in FP32 (differences in FP64 first): FP64
-// division is slow on this part.
+// so only the differences are taken in FP64 and the step itself (relative to
+// s1) is formed and safeguarded in FP32: FP64 arithmetic is scarce on this
+// part and every column takes this step a few times.
 __device__ __forceinline__ double sigma_step(double s0, double f0, double s1, double f1) {
-    const double g0 = f0 - s0, g1 = f1 - s1;
-    const float den = (float)(g1 - g0);
+    const float g1 = (float)(f1 - s1), g0 = (float)(f0 - s0), ds = (float)(s1 - s0);
+    const float den = g1 - g0;
     if (den == 0.0f) return f1;
-    const double cand = s1 - g1 * (double)((float)(s1 - s0) / den);
-    const double w = 4.0 * fabs(g1);
-    const double lo = fmin(s1, f1) - w, hi = fmax(s1, f1) + w;
-    return (cand > 0.0 && cand >= lo && cand <= hi) ? cand : f1;
+    const float step = -g1 * (ds / den);                  // candidate - s1
+    const float w = 4.0f * fabsf(g1);
+    const float lo = fminf(0.0f, g1) - w, hi = fmaxf(0.0f, g1) + w;
+    const double cand = s1 + (double)step;
+    return (cand > 0.0 && step >= lo && step <= hi) ? cand : f1;
+}
+
+// sqrt(q) for q > 0 in FP64 by one step of Newton's (Heron's) iteration
+// y <- y + (q - y^2) / (2 y) from the FP32 root: the FP32 root's relative
+// error (at most 2^-23) is squared, so the result is within a few FP64 units
+// of the root, with five FP64 operations.  Outside the FP32 range, sqrt.
+__device__ __forceinline__ double sqrt_heron(double q) {
+    const float yf = sqrtf((float)q);
+    if (!(yf > 1e-18f && yf < 1e18f)) return sqrt(q);
+    const double y0 = (double)yf;
+    return fma(fma(-y0, y0, q), (double)(0.5f / yf), y0);
 }
 
 // Algorithm 1 for response column j, by one warp: warm start from b = 0,
@@ -598,7 +611,7 @@ __device__ void solve_column(int j, T* __restrict__ g, T* __restrict__ b, int* _
             q = floor2;
             status |= COL_DEGENERATE;
         }
-        const double sn = sqrt(q);
+        const double sn = sqrt_heron(q);
         if (fabs(sn - sigma) < a.tol) {
             sigma = sn;
             break;
@@ -659,12 +672,13 @@ struct Support {
 };
 
 // Shared memory of one lazy-solver warp: the support list, the chunk
-// summaries, the support's block of S, and the last sigma step (sigma,
-// F(sigma)) for the secant step (kept out of registers).
+// summaries, the support's block of S, the last sigma step (sigma,
+// F(sigma)) for the secant step (kept out of registers) and the support the
+// block of S was gathered for.
 template <typename T>
 __host__ __device__ constexpr size_t lazy_warp_smem_bytes(int ldp) {
     return (size_t)LAZY_CAP * (sizeof(int) + sizeof(T)) + (size_t)num_chunks(ldp) * sizeof(ChunkInfo) +
-           (size_t)ACT_MAX * ACT_MAX * sizeof(T) + 2 * sizeof(double);
+           (size_t)ACT_MAX * ACT_MAX * sizeof(T) + 2 * sizeof(double) + ACT_MAX * sizeof(int);
 }
 
 // Set b_k = v in the sorted support (insert, update or remove).  pos is the
@@ -889,27 +903,44 @@ __device__ T sweep_column_lazy(int j, Support<T>& s, const CDArgs<T>& a, T lam,
 // coordinate order) over the current support A only, until a sweep moves no
 // coefficient by tol or more (at most maxit sweeps).  Lane m holds coordinate
 // A_m: its b and g_m = S_jm - sum_{l in A} S_ml b_l; the block S_AA is
-// gathered once into shared memory (column k at saa + k ACT_MAX).  The
-// phase's net change of b enters the column's running sums as one change, so
-// the chunk skip test stays exact for the coordinates outside A.  Coordinates that reach zero leave the
-// support and mark their chunk for a rescan.  Returns the sweeps done (0 when
-// A is empty or larger than ACT_MAX); `conv` tells whether the last sweep
-// moved nothing by tol (true for an empty A, false when A is too large).
+// gathered into shared memory (column k at saa + k ACT_MAX), and kept from
+// the column's last phase when A is the same (saa_list, saa_n).  The phase's
+// net change of b enters the column's running sums as one change, so the
+// chunk skip test stays exact for the coordinates outside A.  Coordinates
+// that reach zero leave the support and mark their chunk for a rescan.  One
+// move is the phase's critical path: every lane forms its candidate, one
+// shuffle broadcasts the owner's change, and every lane updates its gradient
+// with the column of S_AA loaded one move ahead (a zero change adds exact
+// zeros, so no lane branches on it).  Returns the sweeps done (0 when A is
+// empty or larger than ACT_MAX); `conv` tells whether the last sweep moved
+// nothing by tol (true for an empty A, false when A is too large).
 template <typename T, bool STD>
 __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* __restrict__ saa,
-                            unsigned long long& moves, ColScan& cs, bool& conv) {
+                            int* __restrict__ saa_list, int& saa_n, unsigned long long& moves,
+                            ColScan& cs, bool& conv) {
     const int lane = threadIdx.x & 31;
     const int n = s.n;
     conv = n <= ACT_MAX;
     if (n == 0 || n > ACT_MAX) return 0;
     conv = false;
     const int ldp = a.ldp;
-#pragma unroll 8
-    for (int t = lane; t < n * n; t += 32) {
-        const int k = t / n, m = t - k * n;
-        saa[k * ACT_MAX + m] = a.SC[(size_t)s.idx[m] * ldp + s.idx[k]];
-    }
     const int my = lane < n ? s.idx[lane] : 0;
+    if (!(saa_n == n && __all_sync(FULL_MASK, lane >= n || saa_list[lane] == my))) {
+        // lane m reads S_{A_m A_k} for four k at a time (independent loads)
+        for (int k0 = 0; k0 < n; k0 += 4) {
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + u;
+                v[u] = (k < n && lane < n) ? a.SC[(size_t)my * ldp + s.idx[k]] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u < n) saa[(k0 + u) * ACT_MAX + lane] = v[u];
+        }
+        saa_list[lane] = my;
+        saa_n = n;
+    }
     T b = lane < n ? s.val[lane] : T(0);
     const T b_start = b;
     T g = lane < n ? a.SC[(size_t)j * ldp + my] : T(0);
@@ -921,29 +952,30 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
         if (lane < n) g = fma(-saa[l * ACT_MAX + lane], bl, g);
     }
     int sw = 0;
+    unsigned mv = 0;
     while (sw < a.maxit) {
         ++sw;
         T md = T(0);
+        T c = lane < n ? saa[lane] : T(0);                   // column of S_AA for k = 0
         for (int k = 0; k < n; ++k) {
-            T nb = b, d = T(0);
-            if (lane == k) {
-                if constexpr (STD) nb = soft<T>(g + b, lam);                 // S_kk = 1
-                else nb = soft<T>(g + skk * b, lam) / skk;
-                d = nb - b;
-            }
-            d = __shfl_sync(FULL_MASK, d, k);
-            if (d != T(0)) {
-                if (lane < n) g = fma(-saa[k * ACT_MAX + lane], d, g);
-                if (lane == k) b = nb;
-                md = fmax(md, fabs(d));
-                ++moves;
-            }
+            const int kn = k + 1 < n ? k + 1 : k;
+            const T cn = lane < n ? saa[kn * ACT_MAX + lane] : T(0);   // next column
+            T nb;
+            if constexpr (STD) nb = soft<T>(g + b, lam);                 // S_kk = 1
+            else nb = soft<T>(g + skk * b, lam) / skk;
+            const T d = __shfl_sync(FULL_MASK, nb - b, k);
+            if (lane == k) b = nb;
+            g = fma(-c, d, g);
+            md = fmax(md, fabs(d));
+            mv += d != T(0);
+            c = cn;
         }
         if ((double)md < a.tol) {
             conv = true;
             break;
         }
     }
+    moves += mv;
     // the phase enters the running sums as one change: its net l1 size
     const float net = warp_sum_f(lane < n ? fabsf((float)(b - b_start)) : 0.f);
     cs.dsum += net * (1.0f + 0x1p-16f);
@@ -965,26 +997,41 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
 
 // sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the sorted support (Eq. (14)).
 // Every product is formed in FP64 (for FP32 data the product of two FP32
-// values is exact in FP64) and every sum is carried in FP64.  Rows u of the
-// support run in turn and the lanes take the columns v, so no lane divides an
-// index; the row sums b_u (sum_v b_v S_uv) keep the FP64 work at one fused
-// multiply-add per pair.
+// values is exact in FP64) and every sum is carried in FP64.  FP64 arithmetic
+// is scarce on this part and every column runs this step a few times, so the
+// FP64 work is kept to a few instructions per lane: the n^2 pairs (u, v) and
+// the n terms of b'S_.j are spread over the lanes (pair indices stepped by
+// 32 without a divide per pair), each lane adds b_u b_v S_uv and -2 b_u S_uj
+// into one FP64 partial, and one FP64 warp sum ends it.
 template <typename T>
 __device__ double residual_quadratic_form_list(int j, const Support<T>& s, const CDArgs<T>& a) {
     const int lane = threadIdx.x & 31;
     const int n = s.n;
-    double lin = 0.0, quad = 0.0;
-    for (int u = lane; u < n; u += 32)
-        lin = fma((double)s.val[u], (double)a.SC[(size_t)s.idx[u] * a.ldp + j], lin);
-    for (int u = 0; u < n; ++u) {
-        const T* __restrict__ row = a.SC + (size_t)s.idx[u] * a.ldp;
-        double part = 0.0;
-        for (int v = lane; v < n; v += 32) part = fma((double)s.val[v], (double)row[s.idx[v]], part);
-        quad = fma((double)s.val[u], part, quad);
+    const int ldp = a.ldp;
+    double acc = 0.0;
+    if (lane < n) {
+        // -2 b_u S_uj for u = lane, lane + 32, ... (-2 b_u is exact in the data precision)
+        for (int u = lane; u < n; u += 32)
+            acc = fma((double)(T(-2) * s.val[u]), (double)a.SC[(size_t)s.idx[u] * ldp + j], acc);
     }
-    lin = warp_sum(lin);
-    quad = warp_sum(quad);
-    return (double)a.SC[(size_t)j * a.ldp + j] - 2.0 * lin + quad;
+    const int np = n * n;
+    if (lane < np) {
+        // pair t = u n + v for t = lane, lane + 32, ...: (u, v) advance by (q, r)
+        int u = lane / n, v = lane - (lane / n) * n;
+        const int q = 32 / n, r = 32 - (32 / n) * n;
+        for (int t = lane; t < np; t += 32) {
+            const double bb = (double)s.val[u] * (double)s.val[v];
+            acc = fma(bb, (double)a.SC[(size_t)s.idx[u] * ldp + s.idx[v]], acc);
+            u += q;
+            v += r;
+            if (v >= n) {
+                v -= n;
+                ++u;
+            }
+        }
+    }
+    acc = warp_sum(acc);
+    return (double)a.SC[(size_t)j * ldp + j] + acc;
 }
 
 // Algorithm 1 for column j with the lazy gradient.  Returns false when the
@@ -1001,6 +1048,8 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
     ColScan cs{reinterpret_cast<ChunkInfo*>(wsm + LAZY_CAP * (sizeof(int) + sizeof(T))), 0.f, 0u};
     T* saa = reinterpret_cast<T*>(cs.ci + num_chunks(a.ldp));
     double* prev = reinterpret_cast<double*>(saa + ACT_MAX * ACT_MAX);   // HS: (sigma, F(sigma))
+    int* saa_list = reinterpret_cast<int*>(prev + 2);    // the support S_AA was gathered for
+    int saa_n = -1;
     reset_chunks(cs, a.ldp);
     if constexpr (STD) {
         // b = 0: the gradient is row j of S^C, whose chunk maxima the
@@ -1032,7 +1081,8 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
             // stop rule of Algorithm 1).
             bool conv;
             if (s.n > a.ovf_supp) return false;          // a heavy column: the block solver
-            cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, cnt.act_moves, cs, conv);
+            cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, saa_list, saa_n, cnt.act_moves,
+                                                  cs, conv);
             const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow, conv,
                                                    (int)(cnt.sweeps - sweeps0));
             ++cnt.sweeps;
@@ -1048,7 +1098,7 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
             q = floor2;
             status |= COL_DEGENERATE;
         }
-        const double sn = sqrt(q);
+        const double sn = sqrt_heron(q);
         if (fabs(sn - sigma) < a.tol) {
             sigma = sn;
             break;
@@ -1705,7 +1755,7 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
             q = floor2;
             status |= COL_DEGENERATE;
         }
-        const double sn = sqrt(q);
+        const double sn = sqrt_heron(q);
         if (fabs(sn - sigma) < a.tol) {
             sigma = sn;
             break;
