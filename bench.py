@@ -700,6 +700,34 @@ def er10_block(dev, steps: int, warmup: int):
             "fits_per_step": 10, "seeds": "0-9", "precision": BATCH_PREC, "warps_per_block": w}
 
 
+def run_batch256_steps(args):
+    """The batched workload's steps alone (for profiling): warm-up and timed
+    graph replays of the 256-fit mixed batch, nothing else."""
+    import torch
+    import paper_2203_15031_gb300 as sp
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sp.lib()
+    probs = batch_problems()
+    inputs = [(torch.from_numpy(pr.X).to(dev), pr.lambda0) for pr in probs]
+    bt = sp.Batch(inputs, kind="X", precision=BATCH_PREC, tol=TOL, maxit=MAXIT, use_graph=True)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bt.run(stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        bt.run(stream)
+    b.record(stream)
+    statuses, st = bt.result(stream)
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"workload": "batch256_steps", "ms_per_step": ms,
+                      "solves_per_s": N_FITS / (ms / 1e3), "ok": sum(x == 0 for x in statuses),
+                      "workload_sha256": workload_sha()}), flush=True)
+    bt.close()
+
+
 def run_er10(args):
     import torch
     import paper_2203_15031_gb300 as sp
@@ -1160,8 +1188,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="default: the 256-fit batch; er10, serve, regression, table4, residual, "
-                         "or a single-fit name of synth.WORKLOADS")
+                    help="default: the 256-fit batch; batch256_steps (its steps alone), er10, "
+                         "serve, regression, table4, residual, or a single-fit name of "
+                         "synth.WORKLOADS")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-fracs", type=float, nargs="+", default=[0.5, 0.9])
@@ -1174,6 +1203,8 @@ def main():
         run_serve(args)
     elif args.workload == "er10":
         run_er10(args)
+    elif args.workload == "batch256_steps":
+        run_batch256_steps(args)
     elif args.workload == "regression":
         run_regression(args)
     elif args.workload == "table4":

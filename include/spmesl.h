@@ -115,7 +115,11 @@ typedef struct {
                                    In any fit a column whose support outgrows the lazy solver's
                                    32-coordinate active-set phase is handed over to it */
     int32_t count_rows;         /* measurement: 1 fills spmesl_stats.rows_moved */
-    int32_t reserved[3];
+    int32_t handover;           /* SPMESL_GRADIENT_AUTO: the lazy solver hands a column to the
+                                   block solver when its support exceeds this at the start of an
+                                   active-set phase (0 = 32, the phase's size; at most 256, above
+                                   32 such columns sweep without the phase) */
+    int32_t reserved[2];
 } spmesl_opts;
 
 typedef struct {
@@ -509,6 +513,50 @@ spmesl_status spmesl_batch_fit_stats(const spmesl_batch* batch, int i, spmesl_st
  * choice is kept in the batch and written to *best_warps. */
 spmesl_status spmesl_batch_tune(spmesl_batch* batch, void* workspace, size_t ws_bytes,
                                 void* stream, int* best_warps);
+
+/*
+ * Launch choice of the batch tuner (not in the paper): warps per block of the
+ * lazy launch, the lazy solver's hand-over support (opts.handover), the fit
+ * size from which heavy columns are routed by heat (opts.heavy_min_p, -1 =
+ * never) and the heat limit, with the step time measured for it.
+ */
+typedef struct {
+    int32_t warps_per_block;
+    int32_t handover;
+    int32_t heavy_min_p;
+    int32_t heavy_heat;
+    float ms;                   /* measured time of one batch run with this choice, ms */
+    int32_t from_cache;         /* 1: read from the cache file, nothing timed */
+} spmesl_tune_choice;
+
+/* Autotune with a persistent cache (not in the paper): with cache_path
+ * non-NULL, a choice stored for this class of batch (spmesl_tune_key) by the
+ * same library version is applied without timing; otherwise the batch is run
+ * for every candidate (warps 4 or 8; hand-over support 32 or 64; heat routing
+ * from p >= 4096, from p >= 1024 or never), the fastest is applied and, with
+ * cache_path, stored.  Runs the batch several times on `workspace` when it
+ * times.  out (host, may be NULL) receives the choice.  Errors: EINVAL, ECUDA. */
+spmesl_status spmesl_batch_tune_cached(spmesl_batch* batch, void* workspace, size_t ws_bytes,
+                                       void* stream, const char* cache_path,
+                                       spmesl_tune_choice* out);
+
+/* A helper (no passage of the paper): the tuning cache's key of a class of
+ * batches: precision, standardisation, SM count and the power-of-two buckets
+ * of the largest p, the mean n and the number of fits.  Writes at most len
+ * bytes to key; returns its length, or -1. */
+int spmesl_tune_key(int precision, int standardize, int sms, int count, int max_p, double mean_n,
+                    char* key, size_t len);
+
+/* A helper (no passage of the paper): the choice stored under key in the
+ * JSON cache file at path by this library version (from_cache = 1), else
+ * ENOTFOUND (no file, no entry, another version, or a malformed file). */
+spmesl_status spmesl_tune_cache_lookup(const char* path, const char* key, spmesl_tune_choice* out);
+
+/* A helper (no passage of the paper): store the choice under key in the cache
+ * file at path (other entries kept; written to a temporary file and renamed).
+ * EINVAL if the file cannot be written or the key holds a quote. */
+spmesl_status spmesl_tune_cache_store(const char* path, const char* key,
+                                      const spmesl_tune_choice* choice);
 
 /* A helper (no passage of the paper): release the batch's host resources
  * (pinned staging, captured graph). */

@@ -32,6 +32,8 @@ __all__ = [
     "spmesl_solve_workspace_bytes",
     "spmesl_solve", "spmesl_batch_create", "spmesl_batch_workspace_bytes", "spmesl_batch_run",
     "spmesl_batch_result", "spmesl_batch_tune", "spmesl_batch_fit_stats", "spmesl_batch_destroy",
+    "spmesl_batch_tune_cached", "spmesl_tune_key", "spmesl_tune_cache_lookup",
+    "spmesl_tune_cache_store", "TuneChoice",
     "Problem", "Batch",
     "spmesl_ctx_create", "spmesl_submit", "spmesl_poll", "spmesl_ctx_query", "spmesl_ctx_destroy",
     "Server",
@@ -55,7 +57,8 @@ class Opts(ctypes.Structure):
                 ("record_phase_times", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("gradient", ctypes.c_int32), ("diagnostics", ctypes.c_int32),
                 ("heavy_heat", ctypes.c_int32), ("heavy_min_p", ctypes.c_int32),
-                ("count_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("count_rows", ctypes.c_int32), ("handover", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Problem(ctypes.Structure):
@@ -82,6 +85,16 @@ class Stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+
+
+class TuneChoice(ctypes.Structure):
+    """spmesl_tune_choice (include/spmesl.h)."""
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("handover", ctypes.c_int32),
+                ("heavy_min_p", ctypes.c_int32), ("heavy_heat", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("from_cache", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Metrics(ctypes.Structure):
@@ -139,6 +152,13 @@ _SIGS = {
                                    ctypes.POINTER(Stats), _vp]),
     "spmesl_batch_tune": (_i32, [_vp, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_int)]),
     "spmesl_batch_fit_stats": (_i32, [_vp, _i32, ctypes.POINTER(Stats)]),
+    "spmesl_batch_tune_cached": (_i32, [_vp, _vp, _sz, _vp, ctypes.c_char_p,
+                                        ctypes.POINTER(TuneChoice)]),
+    "spmesl_tune_key": (_i32, [_i32, _i32, _i32, _i32, _i32, _dbl, ctypes.c_char_p, _sz]),
+    "spmesl_tune_cache_lookup": (_i32, [ctypes.c_char_p, ctypes.c_char_p,
+                                        ctypes.POINTER(TuneChoice)]),
+    "spmesl_tune_cache_store": (_i32, [ctypes.c_char_p, ctypes.c_char_p,
+                                       ctypes.POINTER(TuneChoice)]),
     "spmesl_batch_destroy": (None, [_vp]),
     "spmesl_ctx_create": (_i32, [ctypes.POINTER(ctypes.c_void_p), _sz, _i32, _dbl, _i32,
                                  ctypes.POINTER(Opts)]),
@@ -444,7 +464,7 @@ def fit_residual(X, lambda0, tol=1e-6, maxit=1000, precision="fp32", standardize
 def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=True,
         inner_rule=INNER_COLUMN, lambda_rule=LAMBDA_GIVEN, warps_per_block=0,
         gradient=GRADIENT_AUTO, return_B=False, heavy_heat=0, heavy_min_p=0, diagnostics=False,
-        stream=None):
+        handover=0, stream=None):
     """One fit on a CUDA covariance tensor.  Synchronises and returns
     (Theta, sigma, stats_dict[, B])."""
     import torch
@@ -461,6 +481,7 @@ def fit(S, lambda0, tol=1e-6, maxit=1000, precision="fp32", n=0, standardize=Tru
     opts.heavy_heat = int(heavy_heat)
     opts.heavy_min_p = int(heavy_min_p)
     opts.diagnostics = int(bool(diagnostics))
+    opts.handover = int(handover)
     Theta = torch.empty((p, p), dtype=torch.float64, device=S.device)
     sigma = torch.empty(p, dtype=torch.float64, device=S.device)
     nb = spmesl_fit_workspace_bytes(p, prec)
@@ -513,6 +534,35 @@ def spmesl_batch_fit_stats(batch, i, stats) -> int:
     return lib().spmesl_batch_fit_stats(batch, int(i), ctypes.byref(stats))
 
 
+def spmesl_batch_tune_cached(batch, workspace, ws_bytes, stream=None, cache_path=None):
+    """Returns (status, TuneChoice)."""
+    c = TuneChoice()
+    rc = lib().spmesl_batch_tune_cached(batch, _ptr(workspace), ws_bytes, _stream(stream),
+                                        cache_path.encode() if cache_path else None,
+                                        ctypes.byref(c))
+    return rc, c
+
+
+def spmesl_tune_key(precision, standardize, sms, count, max_p, mean_n) -> str:
+    buf = ctypes.create_string_buffer(256)
+    n = lib().spmesl_tune_key(int(precision), int(standardize), int(sms), int(count), int(max_p),
+                              float(mean_n), buf, 256)
+    if n < 0:
+        raise SpmeslError(SPMESL_EINVAL, "spmesl_tune_key")
+    return buf.value.decode()
+
+
+def spmesl_tune_cache_lookup(path, key):
+    """Returns (status, TuneChoice)."""
+    c = TuneChoice()
+    rc = lib().spmesl_tune_cache_lookup(path.encode(), key.encode(), ctypes.byref(c))
+    return rc, c
+
+
+def spmesl_tune_cache_store(path, key, choice) -> int:
+    return lib().spmesl_tune_cache_store(path.encode(), key.encode(), ctypes.byref(choice))
+
+
 def spmesl_batch_destroy(batch) -> None:
     lib().spmesl_batch_destroy(batch)
 
@@ -527,7 +577,7 @@ class Batch:
     def __init__(self, inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000,
                  use_graph=False, warps_per_block=0, center=False, record_phase_times=False,
                  gradient=GRADIENT_AUTO, heavy_heat=0, heavy_min_p=0, diagnostics=False,
-                 count_rows=False, device=None):
+                 count_rows=False, handover=0, device=None):
         import torch
         _require_cuda()
         prec = _prec(precision)
@@ -560,6 +610,7 @@ class Batch:
         opts.heavy_min_p = int(heavy_min_p)
         opts.diagnostics = int(bool(diagnostics))
         opts.count_rows = int(bool(count_rows))
+        opts.handover = int(handover)
         rc, self.handle = spmesl_batch_create(arr, self.count, tol, maxit, opts)
         _check(rc, "spmesl_batch_create")
         self.ws_bytes = spmesl_batch_workspace_bytes(self.handle)
@@ -568,10 +619,18 @@ class Batch:
     def run(self, stream=None):
         _check(spmesl_batch_run(self.handle, self.ws, self.ws_bytes, stream), "spmesl_batch_run")
 
-    def tune(self, stream=None) -> int:
-        rc, w = spmesl_batch_tune(self.handle, self.ws, self.ws_bytes, stream)
-        _check(rc, "spmesl_batch_tune")
-        return w
+    def tune(self, stream=None, cache=None, full=False):
+        """Autotune the batch's launches.  With neither cache nor full: warps
+        per block only (returns them).  Otherwise the full tuner (warps,
+        hand-over support, heat routing) with the optional cache file path;
+        returns the choice as a dict."""
+        if cache is None and not full:
+            rc, w = spmesl_batch_tune(self.handle, self.ws, self.ws_bytes, stream)
+            _check(rc, "spmesl_batch_tune")
+            return w
+        rc, c = spmesl_batch_tune_cached(self.handle, self.ws, self.ws_bytes, stream, cache)
+        _check(rc, "spmesl_batch_tune_cached")
+        return c.as_dict()
 
     def result(self, stream=None):
         st = Stats()

@@ -17,7 +17,7 @@ using namespace spmesl;
 
 namespace {
 
-constexpr int kVersion = 1 * 10000 + 0 * 100 + 0;
+constexpr int kVersion = 1 * 10000 + 1 * 100 + 0;
 
 bool valid_precision(int prec) {
     return prec == SPMESL_FP64 || prec == SPMESL_FP32 || prec == SPMESL_MIXED;
@@ -263,6 +263,7 @@ spmesl_status spmesl_fit(const void* S, int n, int p, double lambda0, double tol
     f.diagnostics = o.diagnostics ? 1 : 0;
     f.diag_eps = diag_eps_for(o.precision, n);
     f.count_rows = o.count_rows ? 1 : 0;
+    f.handover = o.handover;
     f.Theta = Theta;
     f.sigma_out = sigma;
     f.ws = static_cast<unsigned char*>(workspace);
@@ -406,6 +407,7 @@ spmesl_status spmesl_scaled_lasso(const void* X, const void* y, int n, int p, do
         f.heavy_min_p = o.heavy_min_p;
         f.diagnostics = o.diagnostics ? 1 : 0;
         f.diag_eps = diag_eps_for(o.precision, n);
+        f.handover = o.handover;
         f.Theta = nullptr;
         f.sigma_out = sigma;
         f.ws = ws + L.fit;

@@ -439,6 +439,7 @@ struct spmesl_batch {
     int gradient = SPMESL_GRADIENT_AUTO;
     int heavy_heat = 0, heavy_min_p = 0;   // routing limits of spmesl_opts (0: defaults)
     int diagnostics = 0;           // optimality diagnostics after the coordinate descent
+    int handover = 0;              // the lazy solver's hand-over support (0: default)
     mutable std::vector<spmesl_stats> fit_stats;   // per fit, caller's order (last result)
     size_t off_ovf = 0;            // queue of columns for the eager launch (total_cols ints)
     size_t off_heat = 0, off_order = 0;   // per-column heat and the lazy queue's order
@@ -462,6 +463,7 @@ struct spmesl_batch {
     cudaGraphExec_t graph = nullptr;
     const void* graph_ws = nullptr;
     int graph_W = -1;
+    int graph_key[3] = {0, 0, 0};   // handover, heavy_min_p, heavy_heat of the captured graph
     cudaStream_t cap_stream = nullptr;
     // side stream that zeroes Theta under the coordinate-descent launch
     cudaStream_t side = nullptr;
@@ -579,7 +581,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
         const int lgrid = std::min((b->total_cols + LW - 1) / LW, num_sms() * lper_sm);
         lk<<<lgrid, 32 * LW, lsm, st>>>(fits, colp, count, b->total_cols, b->max_ldp, b->tol,
                                         b->maxit, hdr, ovf, lazy_order ? order : nullptr,
-                                        route ? ACT_MAX : LAZY_CAP);
+                                        route ? handover_of(b->handover) : LAZY_CAP);
         // the columns the lazy launch handed over
         bk<<<bgrid, BLK_THREADS, bsm, st>>>(fits, colp, count, b->tol, b->maxit, hdr, ovf, 1);
         if (heavy && (e = cudaStreamWaitEvent(st, b->join2, 0)) != cudaSuccess) return e;
@@ -750,6 +752,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     b->heavy_min_p = o.heavy_min_p;
     b->diagnostics = o.diagnostics ? 1 : 0;
     b->count_rows = o.count_rows ? 1 : 0;
+    b->handover = o.handover;
     b->tol = tol;
     b->maxit = maxit;
     std::vector<int> order(count);
@@ -909,7 +912,9 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
         return e == cudaSuccess ? SPMESL_OK : SPMESL_ECUDA;
     }
     b->ev_recorded = false;
-    if (!b->graph || b->graph_ws != workspace || b->graph_W != W) {
+    const int gkey[3] = {b->handover, b->heavy_min_p, b->heavy_heat};
+    if (!b->graph || b->graph_ws != workspace || b->graph_W != W ||
+        memcmp(gkey, b->graph_key, sizeof(gkey)) != 0) {
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
@@ -931,6 +936,7 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
         if (e != cudaSuccess) return SPMESL_ECUDA;
         b->graph_ws = workspace;
         b->graph_W = W;
+        memcpy(b->graph_key, gkey, sizeof(gkey));
     }
     return cudaGraphLaunch(b->graph, st) == cudaSuccess ? SPMESL_OK : SPMESL_ECUDA;
 }
@@ -1049,6 +1055,83 @@ spmesl_status spmesl_batch_tune(spmesl_batch* b, void* workspace, size_t ws_byte
     b->use_graph = saved_graph;
     if (best_warps) *best_warps = bestW;
     return best < 1e29f ? SPMESL_OK : SPMESL_ECUDA;
+}
+
+spmesl_status spmesl_batch_tune_cached(spmesl_batch* b, void* workspace, size_t ws_bytes,
+                                       void* stream, const char* cache_path,
+                                       spmesl_tune_choice* out) {
+    if (!b || !workspace) return SPMESL_EINVAL;
+    double nsum = 0.0;
+    int nx = 0;
+    for (const FitPlan& f : b->plan)
+        if (f.X) {
+            nsum += f.n;
+            ++nx;
+        }
+    char key[256];
+    if (spmesl_tune_key(b->precision, b->standardize, num_sms(), b->count, b->max_p,
+                        nx ? nsum / nx : 1.0, key, sizeof(key)) < 0)
+        return SPMESL_EINVAL;
+    spmesl_tune_choice c{};
+    if (cache_path && spmesl_tune_cache_lookup(cache_path, key, &c) == SPMESL_OK) {
+        b->warps_per_block = c.warps_per_block;
+        b->handover = c.handover;
+        b->heavy_min_p = c.heavy_min_p;
+        b->heavy_heat = c.heavy_heat;
+        if (out) *out = c;
+        return SPMESL_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int saved_graph = b->use_graph;
+    b->use_graph = 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return SPMESL_ECUDA;
+    const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
+    const bool route = b->gradient == SPMESL_GRADIENT_AUTO;
+    static const int wl[] = {4, 8}, we[] = {2, 4, 8, 16};
+    static const int hv[] = {32, 64}, mp[] = {0, 1024, -1};
+    const int* ws_ = lazy ? wl : we;
+    const int nw = lazy ? 2 : 4, nh = route ? 2 : 1, nm = (route && b->standardize) ? 3 : 1;
+    float best = 1e30f;
+    spmesl_tune_choice bc{b->warps_per_block, b->handover, b->heavy_min_p, b->heavy_heat, 0.f, 0};
+    bool ok = true;
+    for (int iw = 0; iw < nw && ok; ++iw)
+        for (int ih = 0; ih < nh && ok; ++ih)
+            for (int im = 0; im < nm && ok; ++im) {
+                b->warps_per_block = ws_[iw];
+                if (route) b->handover = hv[ih];
+                if (route && b->standardize) b->heavy_min_p = mp[im];
+                float tot = 0.f;
+                for (int rep = 0; rep < 3 && ok; ++rep) {
+                    cudaEventRecord(e0, st);
+                    ok = spmesl_batch_run(b, workspace, ws_bytes, stream) == SPMESL_OK;
+                    cudaEventRecord(e1, st);
+                    if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0) tot += ms;           // the first run warms up
+                    } else {
+                        ok = false;
+                    }
+                }
+                if (ok && tot / 2 < best) {
+                    best = tot / 2;
+                    bc = spmesl_tune_choice{b->warps_per_block, b->handover, b->heavy_min_p,
+                                            b->heavy_heat, best, 0};
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->warps_per_block = bc.warps_per_block;
+    b->handover = bc.handover;
+    b->heavy_min_p = bc.heavy_min_p;
+    b->use_graph = saved_graph;
+    if (!ok) return SPMESL_ECUDA;
+    if (cache_path && spmesl_tune_cache_store(cache_path, key, &bc) != SPMESL_OK)
+        return SPMESL_EINVAL;
+    if (out) *out = bc;
+    return SPMESL_OK;
 }
 
 void spmesl_batch_destroy(spmesl_batch* b) {

@@ -590,7 +590,7 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     // hold.  Heat overstates the support of small fits, whose slices are cheap
     // anyway, so the routing by heat is kept to large fits.
     const bool route = lazy && f.gradient == SPMESL_GRADIENT_AUTO;
-    a.ovf_supp = route ? ACT_MAX : LAZY_CAP;
+    a.ovf_supp = route ? handover_of(f.handover) : LAZY_CAP;
     auto lk = cd_column_lazy_kernel<T, STD>;
     const size_t lper = lazy_warp_smem_bytes<T>(L.ldp);
     int LW = f.warps_per_block > 0 ? f.warps_per_block : 8;

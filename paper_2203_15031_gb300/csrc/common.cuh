@@ -158,6 +158,7 @@ namespace spmesl {
 // Heavy-column routing limits of spmesl_opts with the defaults applied.
 inline int heavy_heat_of(int v) { return v <= 0 ? 32 : (v > 62 ? 62 : v); }
 inline int heavy_min_p_of(int v) { return v == 0 ? 4096 : (v < 0 ? 0x7fffffff : v); }
+inline int handover_of(int v) { return v <= 0 ? 32 : (v > 256 ? 256 : v); }
 
 cudaError_t launch_gram(const void* X, int n, int p, int ldx, int precision, int center, void* S,
                         int lds, void* ws, cudaStream_t st);
@@ -178,6 +179,7 @@ struct FitLaunch {
     int heavy_min_p = 4096;      // ... in fits of at least this size (< 0: never)
     int diagnostics = 0;         // 1: optimality diagnostics after the coordinate descent
     int count_rows = 0;          // 1: count the distinct coordinates moved per sweep index
+    int handover = 0;            // support above which the lazy solver hands a column over
     double diag_eps = 0.0;       // rounding bound of the working matrix (see diag_eps_for)
     // >= 0: solve only this column (one scaled-lasso regression, lazy column
     // rule) and write its coefficients to beta_out (the p - 1 other columns in
