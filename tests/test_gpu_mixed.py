@@ -97,3 +97,25 @@ def test_hub_p10000_n500_mixed_full_size_sampled():
             want = a if abs(a) <= abs(b) else b
             if abs(abs(a) - abs(b)) > tol:
                 assert abs(Tg[j, k] - want) <= tol and Tg[j, k] == Tg[k, j]
+
+
+def test_hub_p10000_n500_mixed_whole_theta():
+    """The full-size mixed workload against the FP64 oracle over the whole
+    p x p Theta (the oracle runs Algorithm 2 on all columns with OpenMP):
+    max|dTheta| <= 1e-4 max|Theta| and supports agreeing except below 1e-6
+    max|Theta|, the symmetrisation of every pair included."""
+    import os
+    w = synth.WORKLOADS["hub_p10000_n500_mixed"]
+    prob = synth.make_problem("hub", 10000, 500, 0, dtype=np.float32)
+    X = torch.from_numpy(prob.X).to(DEV)
+    S = sp.gram(X, precision="mixed")
+    T, sg, st = sp.fit(S, prob.lambda0, tol=w["tol"], maxit=w["maxit"], precision="mixed")
+    assert st["status"] == sp.SPMESL_OK, st
+    Tg = T.cpu().numpy()
+    del T, S, X
+    torch.cuda.empty_cache()
+    ref = oracle.spmesl(oracle.gram(prob.X.astype(np.float64)), prob.lambda0, tol=w["tol"],
+                        maxit=w["maxit"], nthreads=os.cpu_count() or 1)
+    assert int(ref["worst"]) == oracle.COL_OK
+    res = compare_theta(Tg, ref["Theta"], ref["B"], ref["sigma"])
+    assert res["ok"], res
