@@ -48,6 +48,7 @@ struct BatchFit {
     double lambda0;
     double diag_eps;      // rounding bound of the working matrix (diagnostics)
     unsigned* rows;       // moved-coordinate bitmap of the fit (opts.count_rows) or nullptr
+    double* hand;         // per column the last sigma step at a hand-over (2 doubles)
     int n, p, ldp;
     int col_start, gram_start, theta_start;
     int split_start;      // first block of the batched split/transpose launch
@@ -126,45 +127,86 @@ __global__ void batch_prep_diag_kernel(const BatchFit* __restrict__ fits, int st
     }
 }
 
-// One block per PREP_ROWS rows of one fit (found from the block prefix, so
-// every block has the same work whatever the fit sizes); same arithmetic as
-// the single-fit prep_matrix_kernel; BT is cleared on the side stream.  With heat,
-// also counts per column the off-diagonal entries of the standardised matrix
-// above lambda0: the coordinates that can move in the column's first sweep,
-// a predictor of how long the column takes.  In fits below heavy_min_p
-// columns the count is capped at heavy_heat, so none of their columns is
-// routed to the block solver by heat (the single-fit rule).
-constexpr int PREP_ROWS = 4;
+// The heat order of a batch's columns (decreasing heat, ties in any order:
+// a column's result does not depend on when it runs) as a counting sort over
+// ORDER_BLOCKS blocks: per-block bin counts, then each (bin, block) pair's
+// first position (bins in decreasing heat, blocks in turn), then the scatter.
+constexpr int ORDER_BLOCKS = 128;
+__global__ void __launch_bounds__(256) heat_hist_kernel(const int* __restrict__ heat, int n,
+                                                        int* __restrict__ hist) {
+    __shared__ int bin[HEAT_BINS];
+    for (int t = threadIdx.x; t < HEAT_BINS; t += blockDim.x) bin[t] = 0;
+    __syncthreads();
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        atomicAdd(&bin[min(heat[i], HEAT_BINS - 1)], 1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < HEAT_BINS; t += blockDim.x) hist[blockIdx.x * HEAT_BINS + t] = bin[t];
+}
+
+// One block of HEAT_BINS threads: hist[b][h] becomes the first position of
+// block b's columns of heat h; *n_heavy (if given) the count of heat above
+// heavy_heat.
+__global__ void heat_offsets_kernel(int* __restrict__ hist, int nblocks, int* __restrict__ n_heavy,
+                                    int heavy_heat) {
+    __shared__ int total[HEAT_BINS];
+    const int h = threadIdx.x;
+    int t = 0;
+    for (int b = 0; b < nblocks; ++b) t += hist[b * HEAT_BINS + h];
+    total[h] = t;
+    __syncthreads();
+    int run = 0;
+    for (int g = HEAT_BINS - 1; g > h; --g) run += total[g];
+    if (n_heavy && h == heavy_heat) *n_heavy = run;
+    for (int b = 0; b < nblocks; ++b) {
+        const int v = hist[b * HEAT_BINS + h];
+        hist[b * HEAT_BINS + h] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(256) heat_scatter_kernel(const int* __restrict__ heat, int n,
+                                                           const int* __restrict__ hist,
+                                                           int* __restrict__ order) {
+    __shared__ int cur[HEAT_BINS];
+    for (int t = threadIdx.x; t < HEAT_BINS; t += blockDim.x) cur[t] = hist[blockIdx.x * HEAT_BINS + t];
+    __syncthreads();
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        order[atomicAdd(&cur[min(heat[i], HEAT_BINS - 1)], 1)] = i;
+}
+
+// One warp per row, PREP_ROWS rows per block, the block's rows all of one
+// fit (found from the block prefix), so every block has the same work whatever
+// the fit sizes; same arithmetic as the single-fit prep_matrix_kernel; BT is
+// cleared on the side stream.  With heat, also counts per column the
+// off-diagonal entries of the standardised matrix above lambda0: the
+// coordinates that can move in the column's first sweep, a predictor of how
+// long the column takes.  In fits below heavy_min_p columns the count is
+// capped at heavy_heat, so none of their columns is routed to the block
+// solver by heat (the single-fit rule).
+constexpr int PREP_ROWS = 8;
 template <typename T>
-__global__ void __launch_bounds__(256) batch_prep_matrix_kernel(const BatchFit* __restrict__ fits,
-                                                                const int* __restrict__ prep_prefix,
-                                                                int count, int* __restrict__ heat,
-                                                                int heavy_heat, int heavy_min_p) {
-    __shared__ int wsum[8];
+__global__ void __launch_bounds__(32 * PREP_ROWS) batch_prep_matrix_kernel(
+    const BatchFit* __restrict__ fits, const int* __restrict__ prep_prefix, int count,
+    int* __restrict__ heat, int heavy_heat, int heavy_min_p) {
     const int fi = find_fit(prep_prefix, count, blockIdx.x);
     const BatchFit& f = fits[fi];
-    bool bad = false;
-    const int r0 = (blockIdx.x - f.prep_start) * PREP_ROWS;
-    const int cap = f.p >= heavy_min_p ? INT_MAX : heavy_heat;
-    for (int r = r0; r < min(f.p, r0 + PREP_ROWS); ++r) {
-        int cnt = 0;
-        bad |= standardize_row<T>(static_cast<const T*>(f.S), f.p, f.ldp, r, f.cs, f.csf,
-                                  static_cast<T*>(f.SC), nullptr, nullptr,
-                                  static_cast<T*>(f.diag), threadIdx.x, blockDim.x,
-                                  (T)f.lambda0, heat ? &cnt : nullptr, f.cmax);
-        if (heat) {
-            cnt = __reduce_add_sync(FULL_MASK, cnt);
-            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int t = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-                heat[f.col_start + r] = min(t, cap);
-            }
-            __syncthreads();
-        }
+    const int lane = threadIdx.x & 31;
+    const int r = (blockIdx.x - f.prep_start) * PREP_ROWS + (int)(threadIdx.x >> 5);
+    if (r >= f.p) return;                      // warp-uniform
+    int cnt = 0;
+    const bool bad = standardize_row<T>(static_cast<const T*>(f.S), f.p, f.ldp, r, f.cs, f.csf,
+                                        static_cast<T*>(f.SC), nullptr, nullptr,
+                                        static_cast<T*>(f.diag), lane, 32, (T)f.lambda0,
+                                        heat ? &cnt : nullptr, f.cmax);
+    if (heat) {
+        cnt = __reduce_add_sync(FULL_MASK, cnt);
+        if (lane == 0) heat[f.col_start + r] = min(cnt, f.p >= heavy_min_p ? INT_MAX : heavy_heat);
     }
-    if (bad) set_error(f.ctrl, DEV_ERR_NONFINITE);
+    if (__any_sync(FULL_MASK, bad) && lane == 0) set_error(f.ctrl, DEV_ERR_NONFINITE);
 }
 
 template <typename T>
@@ -192,6 +234,7 @@ __device__ __forceinline__ CDArgs<T> column_args(const BatchFit& f, double tol, 
     a.chunk_max = f.cmax;
     a.rows_moved = f.rows;
     a.rows_words = rows_words(f.p);
+    a.hand = f.hand;
     return a;
 }
 
@@ -396,7 +439,7 @@ struct FitPlan {
     double* Theta;
     double* sigma;
     size_t off_ctrl, off_cs, off_csf, off_sigma, off_status, off_diag, off_cmax, off_mu, off_Sg, off_SC,
-        off_BT, off_rows;
+        off_BT, off_rows, off_hand;
     size_t off_XhT, off_XlT;
     int col_start, gram_start, theta_start, split_start, prep_start;
 };
@@ -443,6 +486,7 @@ struct spmesl_batch {
     mutable std::vector<spmesl_stats> fit_stats;   // per fit, caller's order (last result)
     size_t off_ovf = 0;            // queue of columns for the eager launch (total_cols ints)
     size_t off_heat = 0, off_order = 0;   // per-column heat and the lazy queue's order
+    size_t off_hist = 0;                  // the heat order's per-block bin counts
     std::vector<FitPlan> plan;     // ordered by decreasing p
     size_t off_hdr = 0, off_desc = 0, off_colp = 0, off_gramp = 0, off_thetap = 0, off_ctrls = 0;
     size_t off_prepp = 0;          // block prefix of the standardisation launch
@@ -533,9 +577,13 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     batch_prep_matrix_kernel<T><<<b->total_prep, 256, 0, st>>>(
         fits, reinterpret_cast<const int*>(ws + b->off_prepp), count, lazy_order ? heat : nullptr,
         hheat, heavy_min_p_of(b->heavy_min_p));
-    if (lazy_order)
-        order_by_heat_kernel<<<1, 1024, 0, st>>>(heat, b->total_cols, order,
-                                                 heavy ? &hdr->n_heavy : nullptr, hheat);
+    if (lazy_order) {
+        int* hist = reinterpret_cast<int*>(ws + b->off_hist);
+        heat_hist_kernel<<<ORDER_BLOCKS, 256, 0, st>>>(heat, b->total_cols, hist);
+        heat_offsets_kernel<<<1, HEAT_BINS, 0, st>>>(hist, ORDER_BLOCKS,
+                                                    heavy ? &hdr->n_heavy : nullptr, hheat);
+        heat_scatter_kernel<<<ORDER_BLOCKS, 256, 0, st>>>(heat, b->total_cols, hist, order);
+    }
 
     const size_t budget = (size_t)max_smem_block() - 1024;
     const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
@@ -670,6 +718,7 @@ bool stage_table(spmesl_batch* b, unsigned char* ws) {
         d.lambda0 = f.lambda0;
         d.diag_eps = diag_eps_for(b->precision, f.X ? f.n : 1);
         d.rows = b->count_rows ? reinterpret_cast<unsigned*>(ws + f.off_rows) : nullptr;
+        d.hand = reinterpret_cast<double*>(ws + f.off_hand);
         d.n = f.n;
         d.p = f.p;
         d.ldp = f.ldp;
@@ -802,6 +851,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
         f.off_status = off; off += align_up((size_t)f.p * 4, 256);
         f.off_diag = off;   off += align_up((size_t)f.p * s, 256);
         f.off_cmax = off;   off += align_up((size_t)f.p * row_chunks(f.ldp) * 4, 256);
+        f.off_hand = off;   off += align_up((size_t)f.p * 16, 256);
         if (q.X) {
             f.off_mu = off;  off += align_up((size_t)f.p * s, 256);
             f.off_Sg = off;  off += align_up((size_t)f.p * f.p * s, 256);
@@ -853,6 +903,8 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
     off += align_up(sizeof(int) * (size_t)cols, 256);
     b->off_order = off;
     off += align_up(sizeof(int) * (size_t)cols, 256);
+    b->off_hist = off;
+    off += align_up(sizeof(int) * (size_t)ORDER_BLOCKS * HEAT_BINS, 256);
     b->ws_bytes = off;
     if (spmesl::g_batch_pageable_staging) {
         // used by the serving context: no pinned allocation (whose release can

@@ -579,6 +579,8 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     a.chunk_max = nullptr;
     a.rows_moved = f.count_rows ? reinterpret_cast<unsigned*>(ws + L.rows) : nullptr;
     a.rows_words = rows_words(f.p);
+    // the hand-over record of the column rule lives in the joint rule's G matrix
+    a.hand = reinterpret_cast<double*>(ws + L.GT);
     const bool single = f.response_col >= 0;    // one regression: lazy column rule
     const bool joint = !single && f.inner_rule == SPMESL_INNER_JOINT;
     // Lazy launch shape (warps per block, blocks per SM).

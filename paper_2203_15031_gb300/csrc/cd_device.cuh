@@ -36,6 +36,9 @@ struct CDArgs {
     unsigned* rows_moved;     // measurement (nullptr: off): bit k of row m is set when
                               // coordinate k moved in the m-th full sweep of any column
     int rows_words;           // 32-bit words per row of that bitmap
+    double* hand;             // per column the last sigma step (sigma, F(sigma)) at a hand-over
+                              // from the lazy to the block solver (nullptr: the block solver
+                              // starts every column afresh)
 };
 
 // Full sweeps per column whose moved coordinates are recorded in the bitmap.
@@ -1034,6 +1037,28 @@ __device__ double residual_quadratic_form_list(int j, const Support<T>& s, const
     return (double)a.SC[(size_t)j * ldp + j] + acc;
 }
 
+// The lazy solver's state when it hands column j over: b_j into row j of BT
+// (zero before), sigma, the last sigma step and the step index, so that the
+// block solver continues from this iterate.  Any (b, sigma) is a valid start
+// for the coordinate descent, and the hand-over point depends only on the
+// column's data, so the result is the same wherever the column is solved.
+template <typename T, bool HS>
+__device__ __forceinline__ void hand_over_lazy(int j, const Support<T>& s, const CDArgs<T>& a, double sigma,
+                               double s_prev, double f_prev, int r, int status) {
+    if (!a.hand) return;
+    const int lane = threadIdx.x & 31;
+    T* brow = a.BT + (size_t)j * a.ldp;
+    for (int t = lane; t < s.n; t += 32) brow[s.idx[t]] = s.val[t];
+    if (lane == 0) {
+        a.sigma[j] = sigma;
+        a.hand[2 * (size_t)j] = s_prev;
+        a.hand[2 * (size_t)j + 1] = f_prev;
+        a.col_status[j] = COL_HANDED | (status & (COL_NOT_CONVERGED | COL_DEGENERATE)) |
+                          (r << COL_STEP_SHIFT);
+    }
+    __syncwarp();
+}
+
 // Algorithm 1 for column j with the lazy gradient.  Returns false when the
 // support outgrew the list (nothing written; the caller queues the column
 // for the eager solver).  HS keeps the last sigma step in the warp's shared
@@ -1080,13 +1105,21 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
             // by tol.  Otherwise a full sweep of every coordinate decides (the
             // stop rule of Algorithm 1).
             bool conv;
-            if (s.n > a.ovf_supp) return false;          // a heavy column: the block solver
+            if (s.n > a.ovf_supp) {                       // a heavy column: the block solver
+                hand_over_lazy<T, HS>(j, s, a, sigma, HS ? prev[0] : s_prev, HS ? prev[1] : f_prev,
+                                      r, status);
+                return false;
+            }
             cnt.act_sweeps += active_phase<T, STD>(j, s, a, lam, saa, saa_list, saa_n, cnt.act_moves,
                                                   cs, conv);
             const T md = sweep_column_lazy<T, STD>(j, s, a, lam, cnt.moves, cs, overflow, conv,
                                                    (int)(cnt.sweeps - sweeps0));
             ++cnt.sweeps;
-            if (overflow) return false;
+            if (overflow) {
+                hand_over_lazy<T, HS>(j, s, a, sigma, HS ? prev[0] : s_prev, HS ? prev[1] : f_prev,
+                                      r, status);
+                return false;
+            }
             if ((double)md < a.tol) {
                 inner_ok = true;
                 break;
@@ -1328,6 +1361,7 @@ constexpr int BLK_THREADS = 512;
 constexpr int BLK_WARPS = BLK_THREADS / 32;
 constexpr int BLK_AMAX = 64;       // active-set phase: up to 64 coordinates, two per lane
 constexpr int BLK_LIST = 1024;     // sorted support list (sigma step, phase, g refresh)
+static_assert(LAZY_CAP <= BLK_LIST, "a handed-over support must fit the block solver's list");
 
 // Shared memory of the block solver: g and b (ldp each), S_AA, the support
 // list, the double-buffered candidate moves of the sweep and the support S_AA
@@ -1700,21 +1734,35 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
     int* saa_list = reinterpret_cast<int*>(cand + 2 * 2 * BLK_THREADS);   // support of S_AA
     int saa_n = -1;                                       // warp 0: no S_AA gathered yet
     int par = 0;
+    // a column the lazy solver handed over continues from its iterate
+    const int st0 = a.hand ? a.col_status[j] : COL_OK;
+    const bool warm = (st0 & COL_HANDED) != 0;
     {
         const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
+        const T* __restrict__ brow = a.BT + (size_t)j * ldp;
         for (int k = tid; k < ldp; k += BLK_THREADS) {
             g[k] = Sj[k];                                 // g = S_.j  (b = 0)
-            b[k] = T(0);
+            b[k] = warm ? brow[k] : T(0);
         }
     }
     __syncthreads();
     double sigma = 1.0;                                   // sigma^(0) = 1
     double s_prev = 0.0, f_prev = 0.0;                    // last (sigma, F(sigma))
+    int status = COL_OK;
+    int r0 = 0;
+    bool stale = false;                                   // g is not yet S_.j - S b
+    if (warm) {
+        sigma = a.sigma[j];
+        s_prev = a.hand[2 * (size_t)j];
+        f_prev = a.hand[2 * (size_t)j + 1];
+        status = st0 & (COL_NOT_CONVERGED | COL_DEGENERATE);
+        r0 = st0 >> COL_STEP_SHIFT;
+        stale = true;
+    }
     const unsigned long long sweeps0 = cnt.sweeps;
     const double floor2 = 1e-12 * (double)a.SC[(size_t)j * ldp + j];
-    int status = COL_OK;
     int r;
-    for (r = 0; r < a.maxit; ++r) {
+    for (r = r0; r < a.maxit; ++r) {
         const T lam = (T)(sigma * a.lambda0);
         bool inner_ok = false;
         for (int m = 0; m < a.maxit; ++m) {
@@ -1723,7 +1771,8 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
             // decides (Algorithm 1's stop), as in the lazy solver
             const int n = block_support_list<T>(b, a.p, list, sc, par);
             bool conv = n == 0;
-            if (n > 0 && n <= BLK_AMAX) {
+            const bool phase = n > 0 && n <= BLK_AMAX;
+            if (phase) {
                 int sw = 0;
                 bool c = false;
                 if (tid < 32) sw = block_active_phase<T, STD>(j, b, list, n, a, lam, saa, saa_list,
@@ -1737,8 +1786,12 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
                 conv = sc.red[par][1] != 0;
                 par ^= 1;
                 cnt.act_sweeps += sw;
+            }
+            // a handed-over support (at most LAZY_CAP entries) fits the list
+            if (phase || stale) {
                 block_form_gradient<T>(j, g, b, list, n, a);
                 __syncthreads();
+                stale = false;
             }
             const T md = block_sweep<T, STD>(j, g, b, a, lam, conv, cand, cnt.moves, sc, par,
                                              (int)(cnt.sweeps - sweeps0));

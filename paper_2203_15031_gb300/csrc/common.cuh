@@ -15,6 +15,10 @@ constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr int COL_OK = 0;
 constexpr int COL_NOT_CONVERGED = 1;
 constexpr int COL_DEGENERATE = 2;
+// Set by the lazy solver when it hands a column to the block solver; the bits
+// from COL_STEP_SHIFT up hold the sigma step it was in.
+constexpr int COL_HANDED = 4;
+constexpr int COL_STEP_SHIFT = 8;
 
 // Device-side error codes stored in FitCtrl::err (0 = none).
 constexpr int DEV_ERR_NONFINITE = 1;
