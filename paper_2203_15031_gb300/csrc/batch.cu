@@ -180,11 +180,11 @@ __global__ void __launch_bounds__(256) heat_scatter_kernel(const int* __restrict
 
 // One warp per row, PREP_ROWS rows per block, the block's rows all of one
 // fit (found from the block prefix), so every block has the same work whatever
-// the fit sizes; same arithmetic as the single-fit prep_matrix_kernel; BT is
-// cleared on the side stream.  With heat, also counts per column the
-// off-diagonal entries of the standardised matrix above lambda0: the
-// coordinates that can move in the column's first sweep, a predictor of how
-// long the column takes.  In fits below heavy_min_p columns the count is
+// the fit sizes; same arithmetic as the single-fit prep_matrix_kernel (BT
+// needs no clearing: every solver writes its whole row).  With heat, also
+// counts per column the off-diagonal entries of the standardised matrix
+// above lambda0: the coordinates that can move in the column's first sweep,
+// a predictor of how long the column takes.  In fits below heavy_min_p columns the count is
 // capped at heavy_heat, so none of their columns is routed to the block
 // solver by heat (the single-fit rule).
 constexpr int PREP_ROWS = 8;
@@ -388,33 +388,6 @@ __global__ void __launch_bounds__(32 * BATCH_DIAG_WARPS) batch_diag_kernel(
     }
 }
 
-// Zero every fit's Theta (what = 0) or coefficient rows BT (what = 1;
-// elem bytes per element), with 16-byte stores where aligned.  Both run on
-// a side stream: BT under the Gram and the standardisation (the
-// coordinate-descent launch waits for it), Theta under the
-// coordinate-descent launch, which leaves HBM idle.  The Theta kernel then
-// writes only the nonzero entries.
-__global__ void batch_zero_kernel(const BatchFit* __restrict__ fits, int count, int what,
-                                  int elem) {
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (int fi = 0; fi < count; ++fi) {
-        const BatchFit& f = fits[fi];
-        unsigned char* base = what == 0 ? reinterpret_cast<unsigned char*>(f.Theta)
-                                        : static_cast<unsigned char*>(f.BT);
-        const size_t bytes = what == 0 ? sizeof(double) * (size_t)f.p * f.p
-                                       : (size_t)elem * f.p * f.ldp;
-        const size_t head = (16 - (reinterpret_cast<uintptr_t>(base) & 15)) & 15;
-        const size_t h = head < bytes ? head : bytes;
-        if (tid < h) base[tid] = 0;
-        float4* q = reinterpret_cast<float4*>(base + h);
-        const size_t nq = (bytes - h) / 16;
-        for (size_t i = tid; i < nq; i += stride) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const size_t tail = h + nq * 16;
-        if (tid < bytes - tail) base[tail + tid] = 0;
-    }
-}
-
 template <typename T>
 __global__ void batch_theta_kernel(const BatchFit* __restrict__ fits,
                                    const int* __restrict__ theta_prefix, int count) {
@@ -509,10 +482,7 @@ struct spmesl_batch {
     int graph_W = -1;
     int graph_key[3] = {0, 0, 0};   // handover, heavy_min_p, heavy_heat of the captured graph
     cudaStream_t cap_stream = nullptr;
-    // side stream that zeroes Theta under the coordinate-descent launch
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr, join_bt = nullptr;
-    // second side stream: the block solver's launch over the heavy columns
+    // side stream: the block solver's launch over the heavy columns
     cudaStream_t side2 = nullptr;
     cudaEvent_t fork2 = nullptr, join2 = nullptr;
     // record_phase_times (runs without a graph): events around the CD launch
@@ -542,14 +512,6 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
         (e = cudaMemsetAsync(ws + b->off_rows, 0, b->rows_bytes, st)) != cudaSuccess)
         return e;
     const int count = b->count;
-    // fork: Theta is zeroed on the side stream while the fits run
-    if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(b->side, b->fork, 0)) != cudaSuccess)
-        return e;
-    batch_zero_kernel<<<num_sms() * 4, 256, 0, b->side>>>(fits, count, 1, (int)sizeof(T));
-    if ((e = cudaEventRecord(b->join_bt, b->side)) != cudaSuccess) return e;
-    batch_zero_kernel<<<num_sms() * 4, 256, 0, b->side>>>(fits, count, 0, 8);
-    if ((e = cudaEventRecord(b->join, b->side)) != cudaSuccess) return e;
     if (b->any_x) {
         if (b->center)
             batch_mean_kernel<T><<<dim3((b->max_p + 255) / 256, count), 256, 0, st>>>(fits);
@@ -588,7 +550,6 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     const size_t budget = (size_t)max_smem_block() - 1024;
     const bool lazy = b->gradient != SPMESL_GRADIENT_EAGER;
     int* ovf = reinterpret_cast<int*>(ws + b->off_ovf);
-    if ((e = cudaStreamWaitEvent(st, b->join_bt, 0)) != cudaSuccess) return e;   // BT is zero
     const bool timed = b->record_phase_times && b->ev[0];
     if (timed) cudaEventRecord(b->ev[0], st);
     if (lazy) {
@@ -605,7 +566,7 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
             return e;
         const int bgrid = num_sms() * std::max(1, std::min(bper_sm, 2));
         if (heavy) {
-            // the heavy columns start first, on the second side stream, beside the lazy launch
+            // the heavy columns start first, on the side stream, beside the lazy launch
             if ((e = cudaEventRecord(b->fork2, st)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(b->side2, b->fork2, 0)) != cudaSuccess)
                 return e;
@@ -665,7 +626,6 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
                                                num_sms() * 4));
         dk<<<dgrid, 32 * BATCH_DIAG_WARPS, dsm, st>>>(fits, colp, count, b->total_cols);
     }
-    if ((e = cudaStreamWaitEvent(st, b->join, 0)) != cudaSuccess) return e;   // join
     batch_theta_kernel<T><<<b->total_theta, dim3(32, 8), 0, st>>>(fits, thetap, count);
     return cudaGetLastError();
 }
@@ -940,12 +900,8 @@ spmesl_status spmesl_batch_run(spmesl_batch* b, void* workspace, size_t ws_bytes
         }
     }
     const int W = b->warps_per_block > 0 ? b->warps_per_block : auto_warps(b);
-    if (!b->side) {
-        if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->join_bt, cudaEventDisableTiming) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&b->side2, cudaStreamNonBlocking) != cudaSuccess ||
+    if (!b->side2) {
+        if (cudaStreamCreateWithFlags(&b->side2, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->join2, cudaEventDisableTiming) != cudaSuccess)
             return SPMESL_ECUDA;
@@ -1190,10 +1146,6 @@ void spmesl_batch_destroy(spmesl_batch* b) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->side) cudaStreamDestroy(b->side);
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->join) cudaEventDestroy(b->join);
-    if (b->join_bt) cudaEventDestroy(b->join_bt);
     if (b->side2) cudaStreamDestroy(b->side2);
     if (b->fork2) cudaEventDestroy(b->fork2);
     if (b->join2) cudaEventDestroy(b->join2);

@@ -392,22 +392,6 @@ __global__ void theta_kernel(const T* __restrict__ BT, int p, int ldp,
     theta_pair<T>(BT, p, ldp, sigma, cs, Theta, sigma_out, ctrl, blockIdx.x);
 }
 
-// Zero n doubles (16-byte stores where aligned): Theta before the sparse
-// Theta kernel.  Does nothing when the fit reported a device-side error
-// (non-finite input): Theta is then left as the caller gave it.
-__global__ void zero_kernel(double* __restrict__ x, size_t n, const FitCtrl* ctrl) {
-    if (*reinterpret_cast<const volatile int*>(&ctrl->err) != 0) return;
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        double2* x2 = reinterpret_cast<double2*>(x);
-        for (size_t i = tid; i < n / 2; i += stride) x2[i] = make_double2(0.0, 0.0);
-        if ((n & 1) && tid == 0) x[n - 1] = 0.0;
-    } else {
-        for (size_t i = tid; i < n; i += stride) x[i] = 0.0;
-    }
-}
-
 // One regression r (spmesl_scaled_lasso): beta over the other columns in
 // order, in the original scale (b^o_k = b^C_k c_k / c_r, proof of
 // Proposition 1), sigma^o = sigma^C / c_r, nonzero coefficients counted.
@@ -624,7 +608,10 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
     if ((e = cudaMemsetAsync(ctrl, 0, sizeof(FitCtrl), st)) != cudaSuccess) return e;
     if (heat && (e = cudaMemsetAsync(heat, 0, sizeof(int) * (size_t)f.p, st)) != cudaSuccess)
         return e;
-    if ((e = cudaMemsetAsync(ws + L.BT, 0, (size_t)f.p * L.ldp * sizeof(T), st)) != cudaSuccess)
+    // the joint rule keeps B in memory from B = 0; the column solvers write
+    // every row of B whole
+    if (joint &&
+        (e = cudaMemsetAsync(ws + L.BT, 0, (size_t)f.p * L.ldp * sizeof(T), st)) != cudaSuccess)
         return e;
     if (a.rows_moved &&
         (e = cudaMemsetAsync(a.rows_moved, 0, rows_bitmap_bytes(f.p), st)) != cudaSuccess)
@@ -741,7 +728,6 @@ static cudaError_t run_fit(const FitLaunch& f, const FitLayout& L, cudaStream_t 
         if (f.phase_events) cudaEventRecord(f.phase_events[2], st);
         return cudaGetLastError();
     }
-    zero_kernel<<<g_num_sms * 4, 256, 0, st>>>(f.Theta, (size_t)f.p * f.p, ctrl);
     theta_kernel<T><<<theta_pairs<T>(f.p), dim3(32, 8), 0, st>>>(a.BT, f.p, L.ldp, a.sigma,
                                        reinterpret_cast<const double*>(ws + L.cs), f.Theta,
                                        f.sigma_out, ctrl);

@@ -1037,8 +1037,21 @@ __device__ double residual_quadratic_form_list(int j, const Support<T>& s, const
     return (double)a.SC[(size_t)j * ldp + j] + acc;
 }
 
-// The lazy solver's state when it hands column j over: b_j into row j of BT
-// (zero before), sigma, the last sigma step and the step index, so that the
+// b_j as the whole row j of BT, zeros included (16-byte stores; ldp is a
+// multiple of 32), so BT needs no clearing before the fit.
+template <typename T>
+__device__ __forceinline__ void store_row_lazy(int j, const Support<T>& s, const CDArgs<T>& a) {
+    const int lane = threadIdx.x & 31;
+    T* brow = a.BT + (size_t)j * a.ldp;
+    uint4* q = reinterpret_cast<uint4*>(brow);
+    const int nq = a.ldp * (int)sizeof(T) / 16;
+    for (int i = lane; i < nq; i += 32) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    for (int t = lane; t < s.n; t += 32) brow[s.idx[t]] = s.val[t];
+}
+
+// The lazy solver's state when it hands column j over: b_j as row j of BT,
+// sigma, the last sigma step and the step index, so that the
 // block solver continues from this iterate.  Any (b, sigma) is a valid start
 // for the coordinate descent, and the hand-over point depends only on the
 // column's data, so the result is the same wherever the column is solved.
@@ -1047,8 +1060,7 @@ __device__ __forceinline__ void hand_over_lazy(int j, const Support<T>& s, const
                                double s_prev, double f_prev, int r, int status) {
     if (!a.hand) return;
     const int lane = threadIdx.x & 31;
-    T* brow = a.BT + (size_t)j * a.ldp;
-    for (int t = lane; t < s.n; t += 32) brow[s.idx[t]] = s.val[t];
+    store_row_lazy<T>(j, s, a);
     if (lane == 0) {
         a.sigma[j] = sigma;
         a.hand[2 * (size_t)j] = s_prev;
@@ -1156,9 +1168,7 @@ __device__ bool solve_column_lazy(int j, unsigned char* wsm, const CDArgs<T>& a,
         r = a.maxit - 1;
         status |= COL_NOT_CONVERGED;
     }
-    // b_j into row j of BT (zeroed before the fit)
-    T* brow = a.BT + (size_t)j * a.ldp;
-    for (int t = lane; t < s.n; t += 32) brow[s.idx[t]] = s.val[t];
+    store_row_lazy<T>(j, s, a);
     if (lane == 0) {
         a.sigma[j] = sigma;
         a.col_status[j] = status;
@@ -1858,10 +1868,9 @@ __device__ __forceinline__ void flush_counters_block(FitCtrl* ctrl, ColCounters&
 // tile of rows j0.., columns k0.. (j0 <= k0) and its mirror.  Omega_1 = -B D
 // on the working scale, min-magnitude symmetrisation (for j < k a tie keeps
 // omega_jk) and Omega^o = C Omega C.  Both coefficient tiles are read once
-// into shared memory.  Theta must be zero on entry (the launchers clear it
-// with a memset, a pure streaming write): only the diagonal and the pairs
-// with a nonzero coefficient are written, both entries of a pair with the
-// same value, so Theta is exactly symmetric.  Blocks of the first
+// into shared memory, and every entry of both Theta tiles is written, both
+// entries of a pair with the same value, so Theta is exactly symmetric and
+// needs no clearing beforehand.  Blocks of the first
 // tile row also write sigma in the original scale; nonzero coefficients are
 // counted into ctrl->nnz.  Block shape 32 x 8.  TS = 64 for FP32
 // coefficients, 32 for FP64 (static shared memory).
@@ -1942,23 +1951,32 @@ __device__ void theta_pair(const T* __restrict__ BT, int p, int ldp,
         else out = fabs(okj) > fabs(ojk) ? ojk : okj;  // pair (k, j) with k < j
         return out * (c_j[jj] * c_k[kk]);
     };
-    // Theta is zeroed before the launch: only the diagonal and the pairs with
-    // a nonzero coefficient are written, each pair's two entries by the same
-    // thread (on the diagonal tile both orders of a pair are visited and
-    // write the same value)
+    // Every entry of the tile and of its mirror is written (Theta needs no
+    // clearing first), each row segment by consecutive lanes.  Both entries
+    // of a pair come from the same value(jj, kk), so Theta is exactly
+    // symmetric; a diagonal tile is its own mirror and is written once.
     unsigned long long nnz = 0;
-    for (int jj = ty; jj < TS; jj += 8)
+    for (int jj = ty; jj < TS; jj += 8) {
+        const int j = j0 + jj;
+        if (j >= p) break;
         for (int kk = tx; kk < TS; kk += 32) {
-            const int j = j0 + jj, k = k0 + kk;
-            if (j >= p || k >= p) continue;
-            const bool nz_kj = tB[jj][kk] != T(0), nz_jk = tA[kk][jj] != T(0);
-            nnz += (j != k && nz_kj) + (j0 != k0 && nz_jk);
-            if (j == k || nz_kj || nz_jk) {
-                const double v = value(jj, kk);
-                Theta[(size_t)j * p + k] = v;
-                Theta[(size_t)k * p + j] = v;
+            const int k = k0 + kk;
+            if (k >= p) break;
+            nnz += (j != k && tB[jj][kk] != T(0)) + (j0 != k0 && tA[kk][jj] != T(0));
+            Theta[(size_t)j * p + k] = value(jj, kk);
+        }
+    }
+    if (j0 != k0) {
+        for (int kk = ty; kk < TS; kk += 8) {
+            const int k = k0 + kk;
+            if (k >= p) break;
+            for (int jj = tx; jj < TS; jj += 32) {
+                const int j = j0 + jj;
+                if (j >= p) break;
+                Theta[(size_t)k * p + j] = value(jj, kk);
             }
         }
+    }
     if (j0 == 0 && lin < TS && k0 + lin < p) sigma_out[k0 + lin] = sigma[k0 + lin] / cs[k0 + lin];
     // one atomic per warp
 #pragma unroll

@@ -470,21 +470,6 @@ __global__ void res_theta_kernel(const T* __restrict__ BT, int p, int ldp,
     theta_pair<T>(BT, p, ldp, sigma, cs, Theta, sigma_out, ctrl, blockIdx.x);
 }
 
-// Zero Theta before the sparse Theta kernel; nothing when the fit reported a
-// device-side error (non-finite data): Theta is then left as the caller gave it.
-__global__ void res_zero_kernel(double* __restrict__ x, size_t n, const FitCtrl* ctrl) {
-    if (*reinterpret_cast<const volatile int*>(&ctrl->err) != 0) return;
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        double2* x2 = reinterpret_cast<double2*>(x);
-        for (size_t i = tid; i < n / 2; i += stride) x2[i] = make_double2(0.0, 0.0);
-        if ((n & 1) && tid == 0) x[n - 1] = 0.0;
-    } else {
-        for (size_t i = tid; i < n; i += stride) x[i] = 0.0;
-    }
-}
-
 template <typename T, bool STD>
 cudaError_t run_residual(const ResLaunch& f, const ResLayout& L, cudaStream_t st) {
     int dev = 0, nsm = 0, smem_optin = 0;
@@ -548,7 +533,6 @@ cudaError_t run_residual(const ResLaunch& f, const ResLayout& L, cudaStream_t st
     kern<<<grid, 32 * LW, smem, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (f.phase_events) cudaEventRecord(f.phase_events[1], st);
-    res_zero_kernel<<<nsm * 4, 256, 0, st>>>(f.Theta, (size_t)f.p * f.p, ctrl);
     res_theta_kernel<T><<<theta_pairs<T>(f.p), dim3(32, 8), 0, st>>>(
         a.BT, f.p, L.ldp, a.sigma, cs, f.Theta, f.sigma_out, ctrl);
     if (f.phase_events) cudaEventRecord(f.phase_events[2], st);
