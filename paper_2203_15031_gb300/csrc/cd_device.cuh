@@ -434,6 +434,7 @@ __device__ double residual_quadratic_form(int j, const T* __restrict__ b, const 
 // off-diagonal |SC_rk| (row r of a p x num_chunks(ldp) table; S^C is
 // symmetric, so it is also column r's first-sweep gradient bound).  Returns
 // true if a non-finite entry was seen.
+constexpr int STD_U = 4;
 template <typename T>
 __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, int ldp, int r,
                                                 const double* __restrict__ cs,
@@ -450,70 +451,82 @@ __device__ __forceinline__ bool standardize_row(const T* __restrict__ S, int p, 
     T* __restrict__ grow = GT ? GT + (size_t)r * ldp : nullptr;
     T* __restrict__ brow = BT ? BT + (size_t)r * ldp : nullptr;
     const int nch = num_chunks(ldp);
+    const int wstep = nthr >> 5;
     // 16-byte accesses when the rows of S are 16-byte aligned (same arithmetic)
     const bool vec = sizeof(T) == 4 && (p & 3) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
-    for (int ch = tid >> 5; ch < nch; ch += nthr >> 5) {
-        const int c0 = ch * CHUNK;
-        float mx = 0.f;
-        if constexpr (sizeof(T) == 4) {
-            if (vec) {
-                const int c = c0 + 4 * lane;
-                if (c < ldp) {                        // ldp % 4 == 0: the quad is inside the row
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (c < p) {                      // p % 4 == 0: the whole quad is inside
-                        const float4 sv = *reinterpret_cast<const float4*>(srow + c);
-                        const float4 cc = *reinterpret_cast<const float4*>(csf + c);
-                        bad |= !isfinite(sv.x) || !isfinite(sv.y) || !isfinite(sv.z) || !isfinite(sv.w);
-                        v = make_float4(sv.x * cr * cc.x, sv.y * cr * cc.y, sv.z * cr * cc.z,
-                                        sv.w * cr * cc.w);
-                        const float e[4] = {v.x, v.y, v.z, v.w};
+    // STD_U chunks per pass: their S values are loaded first, so a warp has
+    // STD_U loads in flight instead of one
+    for (int chb = tid >> 5; chb < nch; chb += STD_U * wstep) {
+        T sv[STD_U][4];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            if (c + t == r) {
-                                diag[r] = e[t];
-                            } else {
-                                mx = fmaxf(mx, fabsf(e[t]));
-                                if (heat && fabsf(e[t]) > heat_lam) ++*heat;
-                            }
-                        }
+        for (int u = 0; u < STD_U; ++u) {
+            const int ch = chb + u * wstep;
+            const int c0 = ch * CHUNK;
+            bool done = false;
+            if constexpr (sizeof(T) == 4) {
+                if (vec) {                            // lane: coordinates c0 + 4 lane + t
+                    const int c = c0 + 4 * lane;
+                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ch < nch && c < p) q = *reinterpret_cast<const float4*>(srow + c);
+                    sv[u][0] = q.x; sv[u][1] = q.y; sv[u][2] = q.z; sv[u][3] = q.w;
+                    done = true;
+                }
+            }
+            if (!done) {                              // lane: coordinates c0 + lane + 32 t
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int c = c0 + lane + 32 * t;
+                    sv[u][t] = (ch < nch && c < p) ? srow[c] : T(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < STD_U; ++u) {
+            const int ch = chb + u * wstep;
+            if (ch >= nch) break;                     // warp-uniform
+            const int c0 = ch * CHUNK;
+            float mx = 0.f;
+            T v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int c = vec ? c0 + 4 * lane + t : c0 + lane + 32 * t;
+                v[t] = T(0);
+                if (c < p) {
+                    bad |= !isfinite(sv[u][t]);
+                    const T cc = sizeof(T) == 4 ? (T)csf[c] : (T)cs[c];
+                    v[t] = sv[u][t] * cr * cc;
+                    if (c == r) {
+                        diag[r] = v[t];
+                    } else {
+                        mx = fmaxf(mx, (float)fabs(v[t]));
+                        if (heat && fabs(v[t]) > heat_lam) ++*heat;
                     }
-                    *reinterpret_cast<float4*>(out + c) = v;
-                    if (grow) *reinterpret_cast<float4*>(grow + c) = v;
+                }
+            }
+            if (vec) {                                // ldp % 4 == 0: the quad is inside the row
+                const int c = c0 + 4 * lane;
+                if (c < ldp) {
+                    const float4 q = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+                    *reinterpret_cast<float4*>(out + c) = q;
+                    if (grow) *reinterpret_cast<float4*>(grow + c) = q;
                     if (brow) *reinterpret_cast<float4*>(brow + c) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                if (cmax) {
+            } else {
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
-                    if (lane == 0) cmax[(size_t)r * nch + ch] = mx;
-                }
-                continue;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int c = c0 + lane + 32 * t;
-            if (c >= ldp) break;
-            T v = T(0);
-            if (c < p) {
-                const T sv = srow[c];
-                bad |= !isfinite(sv);
-                const T cc = sizeof(T) == 4 ? (T)csf[c] : (T)cs[c];
-                v = sv * cr * cc;
-                if (c == r) {
-                    diag[r] = v;
-                } else {
-                    mx = fmaxf(mx, (float)fabs(v));
-                    if (heat && fabs(v) > heat_lam) ++*heat;
+                for (int t = 0; t < 4; ++t) {
+                    const int c = c0 + lane + 32 * t;
+                    if (c < ldp) {
+                        out[c] = v[t];
+                        if (grow) grow[c] = v[t];
+                        if (brow) brow[c] = T(0);
+                    }
                 }
             }
-            out[c] = v;
-            if (grow) grow[c] = v;
-            if (brow) brow[c] = T(0);
-        }
-        if (cmax) {
+            if (cmax) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
-            if (lane == 0) cmax[(size_t)r * nch + ch] = mx;
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+                if (lane == 0) cmax[(size_t)r * nch + ch] = mx;
+            }
         }
     }
     return bad;
