@@ -83,7 +83,8 @@ typedef enum {
                                    heat exceeds opts.heavy_heat in fits of at least
                                    opts.heavy_min_p columns (from the start, beside the lazy
                                    launch) and those whose support outgrows the lazy solver's
-                                   32-coordinate active-set phase (after it) */
+                                   32-coordinate active-set phase (after it, continuing from
+                                   the lazy solver's iterate) */
     SPMESL_GRADIENT_EAGER = 1,  /* g_j and b_j stored in shared memory, rank-1 update of the
                                    whole g_j after every coordinate move */
     SPMESL_GRADIENT_LAZY = 2    /* only the support of b_j stored; each 128-coordinate slice of

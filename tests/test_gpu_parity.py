@@ -172,6 +172,39 @@ def test_nonfinite_input_leaves_theta_untouched():
     del keep
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "fp64"])
+def test_stale_workspace_and_theta_do_not_matter(prec):
+    """Neither B^T nor Theta is cleared before a fit: every column solver
+    writes its whole row of B^T and the Theta kernel writes every entry.  A
+    fit whose workspace and Theta start as all-ones bytes (NaN in every float)
+    equals, bit for bit, the same fit started from zeros.  Heat routing from
+    the first column and a small hand-over support send columns through the
+    lazy solver, the block solver and the lazy-to-block hand-over."""
+    dt = np.float64 if prec == "fp64" else np.float32
+    pr = synth.make_problem("hub_scaled", 300, 120, 5, dtype=dt)
+    S = sp.gram(torch.from_numpy(np.ascontiguousarray(pr.X)).to(DEV), precision=prec)
+    p = S.shape[0]
+    opts = sp.spmesl_default_opts()
+    opts.precision = sp._prec(prec)
+    opts.heavy_min_p = 1
+    opts.handover = 8
+    nb = sp.spmesl_fit_workspace_bytes(p, opts.precision)
+    out = []
+    for fill in (0, 0xFF):
+        keep, ws = sp._workspace(nb, DEV)
+        keep.fill_(fill)
+        T = torch.full((p, p), 0.0 if fill == 0 else float("nan"), dtype=torch.float64, device=DEV)
+        sg = torch.empty(p, dtype=torch.float64, device=DEV)
+        st = sp.Stats()
+        rc = sp.spmesl_fit(S, 0, p, pr.lambda0, 1e-6, 1000, opts, T, sg, st, ws, nb)
+        assert rc == sp.SPMESL_OK
+        assert st.block_columns > 0
+        out.append((T.cpu().numpy(), sg.cpu().numpy()))
+        del keep
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def test_iteration_cap_reports_not_converged():
     prob = synth.make_problem("er", 64, 30, 2, dtype=np.float64)
     S = torch.from_numpy(oracle.gram(prob.X)).to(DEV)
