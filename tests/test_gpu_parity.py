@@ -266,6 +266,31 @@ def test_gradient_modes_match_oracle(gradient, prec, standardize):
     _assert_parity(T.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "fp64"])
+def test_warm_handover_matches_oracle(prec):
+    """With a hand-over support of 4 most columns leave the lazy solver in the
+    middle of their solve and the block solver continues from the iterate
+    they leave behind (b_j, sigma, the last secant pair, the step index).
+    The result must still be Algorithm 1's fixed point: parity with the FP64
+    oracle, and the same Theta in a batch as alone."""
+    dt = np.float64 if prec == "fp64" else np.float32
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    prob = synth.make_problem("hub_scaled", 240, 150, 23, dtype=dt)
+    Xd = torch.from_numpy(prob.X).to(DEV)
+    S = sp.gram(Xd, precision=prec)
+    T, sg, st = sp.fit(S, prob.lambda0, tol=tol, maxit=2000, precision=prec, handover=4)
+    assert st["status"] == sp.SPMESL_OK
+    assert st["block_columns"] >= 20
+    _, ref = _oracle_fit(prob.X, prob.lambda0, tol, 2000)
+    _assert_parity(T.cpu().numpy(), ref)
+    bt = sp.Batch([(Xd, prob.lambda0)], kind="X", precision=prec, tol=tol, maxit=2000, handover=4)
+    bt.run()
+    statuses, bst = bt.result()
+    assert statuses[0] == sp.SPMESL_OK and bst["block_columns"] == st["block_columns"]
+    assert np.array_equal(bt.Theta[0].cpu().numpy(), T.cpu().numpy())
+    bt.close()
+
+
 @pytest.mark.parametrize("n,p,seed", [(90, 257, 3), (150, 400, 5)])
 def test_block_solver_batch_equals_single_fits(n, p, seed):
     """Heavy columns run on the block solver in a batch exactly as in a single
