@@ -1370,6 +1370,11 @@ __device__ void diagnose_column(int j, unsigned char* wsm, const CDArgs<T>& a, d
 //    BLK_AMAX coordinates, two per lane, the block S_AA in shared memory)
 //    until a sweep moves nothing by tol; then the block forms g afresh from
 //    row j and the |A| support rows (no drift accumulates across phases);
+//  - working set: after a converged phase one pass over g finds every
+//    coordinate outside A that a sweep with A held would move; none ends the
+//    lasso at this lambda (that sweep would move nothing), else they join A
+//    at b = 0 and the phase runs on the union (while it fits the phase), so
+//    coordinates enter the support without an O(p) update per entry;
 //  - sweep: the cyclic ascending pass of Algorithm 1 over all coordinates (or
 //    with the support held after a converged phase, as in the lazy solver).
 //    Every thread tests its coordinates, a block minimum finds the first
@@ -1384,6 +1389,7 @@ constexpr int BLK_THREADS = 512;
 constexpr int BLK_WARPS = BLK_THREADS / 32;
 constexpr int BLK_AMAX = 64;       // active-set phase: up to 64 coordinates, two per lane
 constexpr int BLK_LIST = 1024;     // sorted support list (sigma step, phase, g refresh)
+constexpr int BLK_WS_ROUNDS = 16;  // working-set rounds (scan, phase on the union) per inner step
 static_assert(LAZY_CAP <= BLK_LIST, "a handed-over support must fit the block solver's list");
 
 // Shared memory of the block solver: g and b (ldp each), S_AA, the support
@@ -1400,6 +1406,8 @@ __host__ __device__ constexpr size_t block_smem_bytes(int ldp) {
 struct BlockScratch {
     int red[2][BLK_WARPS];       // block minimum / counts, double-buffered by parity
     double dred[BLK_WARPS];      // FP64 block sums
+    int vred[BLK_WARPS];         // scan: coordinates that would move, per warp
+    float mred[BLK_WARPS];       // scan: their largest candidate |move|, per warp
     int nlist;
     int col;
 };
@@ -1460,6 +1468,85 @@ __device__ int block_support_list(const T* __restrict__ b, int p, int* __restric
     for (int k = k0; k < k1 && off < BLK_LIST; ++k)
         if (b[k] != T(0)) list[off++] = k;
     __syncthreads();
+    return total;
+}
+
+// The scan that certifies a converged support.  A coordinate k != j outside
+// the support (b_k = 0) would move in a sweep with the support held exactly
+// when its candidate Soft(g_k, lambda) (divided by S_kk without
+// standardisation) is nonzero, i.e. |g_k| > lambda; the candidates are formed
+// as the sweep forms them.  Writes the sorted union of the support and those
+// coordinates into list[0, min(n, BLK_LIST)) and returns n; nv is the number
+// of coordinates that would move and mv the largest |candidate| among them
+// (each taken as if it moved first).  Same segment layout as
+// block_support_list; the block's counts are read before its last barrier,
+// so the single-buffered vred / mred can be written by the next call.
+template <typename T, bool STD>
+__device__ __forceinline__ bool scan_member(int k, int j, const T* __restrict__ g,
+                                            const T* __restrict__ b, const CDArgs<T>& a, T lam,
+                                            T& nb) {
+    const T bk = b[k];
+    nb = T(0);
+    if (bk != T(0)) return true;
+    if (k == j) return false;
+    if constexpr (STD) nb = soft<T>(g[k] + bk, lam);                         // S_kk = 1
+    else nb = soft<T>(g[k] + a.diag[k] * bk, lam) / a.diag[k];
+    return nb != T(0);
+}
+
+template <typename T, bool STD>
+__device__ int block_scan_list(int j, const T* __restrict__ g, const T* __restrict__ b,
+                               const CDArgs<T>& a, T lam, int* __restrict__ list, BlockScratch& sc,
+                               int& par, int& nv, float& mv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = a.p;
+    const int seg = (p + BLK_THREADS - 1) / BLK_THREADS;
+    const int k0 = min(p, (int)threadIdx.x * seg), k1 = min(p, k0 + seg);
+    int c = 0, v = 0;
+    float m = 0.f;
+    for (int k = k0; k < k1; ++k) {
+        T nb;
+        if (scan_member<T, STD>(k, j, g, b, a, lam, nb)) {
+            ++c;
+            if (nb != T(0)) {
+                ++v;
+                m = fmaxf(m, fabsf((float)nb));
+            }
+        }
+    }
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += u;
+    }
+    const int vw = __reduce_add_sync(FULL_MASK, v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL_MASK, m, o));
+    if (lane == 31) sc.red[par][warp] = incl;
+    if (lane == 0) {
+        sc.vred[warp] = vw;
+        sc.mred[warp] = m;
+    }
+    __syncthreads();
+    int off = incl - c, total = 0, vt = 0;
+    float mt = 0.f;
+#pragma unroll
+    for (int w = 0; w < BLK_WARPS; ++w) {
+        const int t = sc.red[par][w];
+        if (w < warp) off += t;
+        total += t;
+        vt += sc.vred[w];
+        mt = fmaxf(mt, sc.mred[w]);
+    }
+    par ^= 1;
+    for (int k = k0; k < k1 && off < BLK_LIST; ++k) {
+        T nb;
+        if (scan_member<T, STD>(k, j, g, b, a, lam, nb)) list[off++] = k;
+    }
+    __syncthreads();
+    nv = vt;
+    mv = mt;
     return total;
 }
 
@@ -1788,11 +1875,14 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
     for (r = r0; r < a.maxit; ++r) {
         const T lam = (T)(sigma * a.lambda0);
         bool inner_ok = false;
+        int rounds = 0;              // working-set rounds at this lambda
+        bool uni = false;            // list[0, nu) holds the union for the next phase
+        int nu = 0;
         for (int m = 0; m < a.maxit; ++m) {
             // converge on the support first (when it fits the phase), then a
             // sweep with the support held decides; otherwise a full sweep
             // decides (Algorithm 1's stop), as in the lazy solver
-            const int n = block_support_list<T>(b, a.p, list, sc, par);
+            int n = uni ? nu : block_support_list<T>(b, a.p, list, sc, par);
             bool conv = n == 0;
             const bool phase = n > 0 && n <= BLK_AMAX;
             if (phase) {
@@ -1812,9 +1902,34 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
             }
             // a handed-over support (at most LAZY_CAP entries) fits the list
             if (phase || stale) {
+                if (uni) n = block_support_list<T>(b, a.p, list, sc, par);   // drop the zeros
                 block_form_gradient<T>(j, g, b, list, n, a);
                 __syncthreads();
                 stale = false;
+            }
+            uni = false;
+            // Working set: with the support converged, one scan of every
+            // coordinate finds those that a sweep with the support held
+            // would move.  None: that sweep would move nothing
+            // (max |delta| = 0), so the lasso at this lambda is solved.
+            // Otherwise, while their union with the support fits the phase
+            // and one of them would move by tol or more, they join the next
+            // phase's coordinates at b = 0, instead of the sweep moving them
+            // one at a time with an O(p) update each.  Else the sweep decides.
+            if (conv && n <= BLK_AMAX && rounds < BLK_WS_ROUNDS) {
+                int nv = 0;
+                float mv = 0.f;
+                nu = block_scan_list<T, STD>(j, g, b, a, lam, list, sc, par, nv, mv);
+                ++cnt.sweeps;
+                if (nv == 0) {
+                    inner_ok = true;
+                    break;
+                }
+                if (nu <= BLK_AMAX && (double)mv >= a.tol) {
+                    uni = true;
+                    ++rounds;
+                    continue;
+                }
             }
             const T md = block_sweep<T, STD>(j, g, b, a, lam, conv, cand, cnt.moves, sc, par,
                                              (int)(cnt.sweeps - sweeps0));
