@@ -1408,6 +1408,8 @@ struct BlockScratch {
     double dred[BLK_WARPS];      // FP64 block sums
     int vred[BLK_WARPS];         // scan: coordinates that would move, per warp
     float mred[BLK_WARPS];       // scan: their largest candidate |move|, per warp
+    int wcnt[2], wmax[2];        // refresh scan: count and largest |move| (float bits), by parity
+    int saa_n;                   // size of the support S_AA was last gathered for (warp 0's copy)
     int nlist;
     int col;
 };
@@ -1550,16 +1552,49 @@ __device__ int block_scan_list(int j, const T* __restrict__ g, const T* __restri
     return total;
 }
 
+// Whether k is one of the sorted list[0, n) (binary search).
+__device__ __forceinline__ bool list_contains(const int* __restrict__ list, int n, int k) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (list[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < n && list[lo] == k;
+}
+
+// The scan of a converged support, folded into the gradient refresh: while
+// g is formed, every coordinate k != j outside list[0, n) with b_k = 0 whose
+// candidate Soft(g_k, lambda) (divided by S_kk without standardisation) is
+// nonzero, i.e. which a sweep with the support held would move, is counted
+// into sc.wcnt[wp] and, while there is room, appended to vlist (in no
+// particular order); sc.wmax[wp] keeps the largest |candidate| (as the bits
+// of a non-negative float).  Thread 0 clears the other parity's pair for
+// the next scan: that pair was last read before a barrier that every thread
+// has passed since.
+struct RefreshScan {
+    int* vlist;
+    int vcap;
+    int wp;
+};
+
 // g = S_.j - sum_{l in A} S_.l b_l over the whole row (block-wide), A = list[0, n).
 // A thread takes QG of its quads at once and reads R support rows for each, so
 // QG * R independent loads are in flight; the products are accumulated in
-// the order of the list.
-template <typename T>
+// the order of the list.  With `scan` the refresh also scans (RefreshScan).
+template <typename T, bool STD>
 __device__ void block_form_gradient(int j, T* __restrict__ g, const T* __restrict__ b,
-                                    const int* __restrict__ list, int n, const CDArgs<T>& a) {
+                                    const int* __restrict__ list, int n, const CDArgs<T>& a,
+                                    bool scan, T lam, BlockScratch& sc, RefreshScan ws) {
     constexpr int QG = sizeof(T) == 4 ? 2 : 1, R = 4;
     const int ldp = a.ldp;
     const T* __restrict__ Sj = a.SC + (size_t)j * ldp;
+    if (scan) {
+        if (threadIdx.x == 0) {
+            sc.wcnt[ws.wp ^ 1] = 0;
+            sc.wmax[ws.wp ^ 1] = 0;
+        }
+    }
     for (int q0 = threadIdx.x; 4 * q0 < ldp; q0 += QG * BLK_THREADS) {
         T acc[QG][4];
 #pragma unroll
@@ -1609,7 +1644,63 @@ __device__ void block_form_gradient(int j, T* __restrict__ g, const T* __restric
 #pragma unroll
                 for (int t = 0; t < 4; ++t) g[k0 + t] = acc[u][t];
         }
+        if (scan) {
+#pragma unroll
+            for (int u = 0; u < QG; ++u) {
+                const int k0 = 4 * (q0 + u * BLK_THREADS);
+                if (k0 < a.p) {
+                    T bq[4];
+                    load4<T>(b + k0, bq);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int k = k0 + t;
+                        if (k < a.p && k != j && bq[t] == T(0)) {
+                            T nb;
+                            if constexpr (STD) nb = soft<T>(acc[u][t] + bq[t], lam);     // S_kk = 1
+                            else nb = soft<T>(acc[u][t] + a.diag[k] * bq[t], lam) / a.diag[k];
+                            if (nb != T(0) && !list_contains(list, n, k)) {
+                                const int slot = atomicAdd(&sc.wcnt[ws.wp], 1);
+                                if (slot < ws.vcap) ws.vlist[slot] = k;
+                                atomicMax(&sc.wmax[ws.wp], __float_as_int(fabsf((float)nb)));
+                            }
+                        }
+                    }
+                }
+            }
+        }
     }
+}
+
+// The sorted union of list[0, n) (sorted) and vlist[0, nv) (distinct, not in
+// the list, in any order) into u[0, n + nv), by warp 0 (n + nv <= BLK_AMAX):
+// an entry's place is the number of entries of both lists below it.
+__device__ inline void warp_union(const int* __restrict__ list, int n, const int* __restrict__ vlist,
+                           int nv, int* __restrict__ u) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h;
+        int x = INT_MAX, cv = 0;
+        if (e < n) x = list[e];
+        int y = INT_MAX, ry = 0;
+        if (e < nv) y = vlist[e];
+        for (int t = 0; t < nv; ++t) {
+            const int w = vlist[t];
+            cv += w < x;
+            ry += w < y;
+        }
+        if (e < n) u[e + cv] = x;
+        if (e < nv) {
+            int lo = 0, hi = n;                       // entries of the list below y
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (list[mid] < y) lo = mid + 1;
+                else hi = mid;
+            }
+            u[ry + lo] = y;
+        }
+    }
+    __syncwarp();
 }
 
 // Active-set phase of the block solver, run by warp 0 on A = list[0, n),
@@ -1794,7 +1885,7 @@ __device__ T block_sweep(int j, T* __restrict__ g, T* __restrict__ b, const CDAr
 // sigma_j^2 = S_jj - 2 b'S_.j + b'S b in FP64 over the support list (block-wide),
 // FP64 products; a support longer than the list takes the rows from b itself.
 template <typename T>
-__device__ double block_quadratic_form(int j, const T* __restrict__ b, const int* __restrict__ list,
+__device__ __noinline__ double block_quadratic_form(int j, const T* __restrict__ b, const int* __restrict__ list,
                                        int n, const CDArgs<T>& a, BlockScratch& sc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ldp = a.ldp, p = a.p;
@@ -1828,6 +1919,40 @@ __device__ double block_quadratic_form(int j, const T* __restrict__ b, const int
     return (double)a.SC[(size_t)j * ldp + j] - 2.0 * lin + quad;
 }
 
+// sigma_j^2 = S_jj - 2 b'S_.j + b'S b (Eq. (14)) in FP64 from the block
+// S_AA in shared memory, when the support lies in the list A it was
+// gathered for (A = saa_list[0, na), sorted; saa[k BLK_AMAX + m] = S_{A_k A_m}):
+// b is zero on A outside the support, and the zero terms add nothing.
+// Returns false (nothing computed) when some support coordinate is not in A.
+// The products are formed in FP64, warp w taking the rows k = w, w + 16, ...
+// of S_AA and each lane two of its entries; one fixed-order block sum.
+template <typename T>
+__device__ __noinline__ bool block_quadratic_form_saa(int j, const T* __restrict__ b, int nsupp,
+                                         const int* __restrict__ saa_list, int na,
+                                         const T* __restrict__ saa, const CDArgs<T>& a,
+                                         BlockScratch& sc, double& q) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
+    if (na <= 0 || na > BLK_AMAX || nsupp > na) return false;
+    const int inA = __syncthreads_count(tid < na && b[saa_list[tid]] != T(0));
+    if (inA != nsupp) return false;
+    const int v0 = lane, v1 = lane + 32;
+    const double bv0 = v0 < na ? (double)b[saa_list[v0]] : 0.0;
+    const double bv1 = v1 < na ? (double)b[saa_list[v1]] : 0.0;
+    double acc = 0.0;
+    for (int k = warp; k < na; k += BLK_WARPS) {
+        const int ak = saa_list[k];
+        const double bk = (double)b[ak];
+        double t = v0 < na ? bv0 * (double)saa[k * BLK_AMAX + v0] : 0.0;
+        if (v1 < na) t = fma(bv1, (double)saa[k * BLK_AMAX + v1], t);
+        acc = fma(bk, t, acc);                              // b_k sum_m S_km b_m
+        if (lane == 0) acc = fma(-2.0 * bk, (double)a.SC[(size_t)ak * a.ldp + j], acc);
+    }
+    acc = block_sum_d(acc, sc);
+    q = (double)a.SC[(size_t)j * a.ldp + j] + acc;
+    return true;
+}
+
 // Algorithm 1 for column j by the whole block (see above).  Writes b_j (the
 // whole row j of BT), sigma_j and the column status.  Counters are kept
 // identically by every thread; the caller flushes thread 0's.
@@ -1842,8 +1967,13 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
     int* list = reinterpret_cast<int*>(saa + BLK_AMAX * BLK_AMAX);
     T* cand = reinterpret_cast<T*>(list + BLK_LIST);
     int* saa_list = reinterpret_cast<int*>(cand + 2 * 2 * BLK_THREADS);   // support of S_AA
+    // the candidate buffers are idle between sweeps: the working set's union
+    // and the refresh scan's coordinates live there
+    int* ubuf = reinterpret_cast<int*>(cand);
+    int* vlist = ubuf + BLK_AMAX;
     int saa_n = -1;                                       // warp 0: no S_AA gathered yet
     int par = 0;
+    int wp = 0;                                           // parity of the refresh scan's counters
     // a column the lazy solver handed over continues from its iterate
     const int st0 = a.hand ? a.col_status[j] : COL_OK;
     const bool warm = (st0 & COL_HANDED) != 0;
@@ -1853,6 +1983,11 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
         for (int k = tid; k < ldp; k += BLK_THREADS) {
             g[k] = Sj[k];                                 // g = S_.j  (b = 0)
             b[k] = warm ? brow[k] : T(0);
+        }
+        if (tid == 0) {
+            sc.wcnt[0] = sc.wcnt[1] = 0;
+            sc.wmax[0] = sc.wmax[1] = 0;
+            sc.saa_n = -1;
         }
     }
     __syncthreads();
@@ -1876,23 +2011,25 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
         const T lam = (T)(sigma * a.lambda0);
         bool inner_ok = false;
         int rounds = 0;              // working-set rounds at this lambda
-        bool uni = false;            // list[0, nu) holds the union for the next phase
+        bool uni = false;            // ubuf[0, nu) holds the union for the next phase
         int nu = 0;
         for (int m = 0; m < a.maxit; ++m) {
             // converge on the support first (when it fits the phase), then a
             // sweep with the support held decides; otherwise a full sweep
             // decides (Algorithm 1's stop), as in the lazy solver
             int n = uni ? nu : block_support_list<T>(b, a.p, list, sc, par);
+            const int* plist = uni ? ubuf : list;
             bool conv = n == 0;
             const bool phase = n > 0 && n <= BLK_AMAX;
             if (phase) {
                 int sw = 0;
                 bool c = false;
-                if (tid < 32) sw = block_active_phase<T, STD>(j, b, list, n, a, lam, saa, saa_list,
+                if (tid < 32) sw = block_active_phase<T, STD>(j, b, plist, n, a, lam, saa, saa_list,
                                                               saa_n, cnt.act_moves, c);
                 if (tid == 0) {
                     sc.red[par][0] = sw;
                     sc.red[par][1] = c ? 1 : 0;
+                    sc.saa_n = saa_n;
                 }
                 __syncthreads();
                 sw = sc.red[par][0];
@@ -1900,14 +2037,6 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
                 par ^= 1;
                 cnt.act_sweeps += sw;
             }
-            // a handed-over support (at most LAZY_CAP entries) fits the list
-            if (phase || stale) {
-                if (uni) n = block_support_list<T>(b, a.p, list, sc, par);   // drop the zeros
-                block_form_gradient<T>(j, g, b, list, n, a);
-                __syncthreads();
-                stale = false;
-            }
-            uni = false;
             // Working set: with the support converged, one scan of every
             // coordinate finds those that a sweep with the support held
             // would move.  None: that sweep would move nothing
@@ -1916,16 +2045,40 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
             // and one of them would move by tol or more, they join the next
             // phase's coordinates at b = 0, instead of the sweep moving them
             // one at a time with an O(p) update each.  Else the sweep decides.
-            if (conv && n <= BLK_AMAX && rounds < BLK_WS_ROUNDS) {
-                int nv = 0;
-                float mv = 0.f;
-                nu = block_scan_list<T, STD>(j, g, b, a, lam, list, sc, par, nv, mv);
+            // After a phase the scan runs inside the gradient refresh.
+            const bool ws = conv && rounds < BLK_WS_ROUNDS;
+            bool scanned = false;
+            int nv = 0;
+            float mv = 0.f;
+            // a handed-over support (at most LAZY_CAP entries) fits the list
+            if (phase || stale) {
+                if (uni) n = block_support_list<T>(b, a.p, list, sc, par);   // the support
+                scanned = ws && n <= BLK_AMAX;
+                block_form_gradient<T, STD>(j, g, b, list, n, a, scanned, lam, sc,
+                                            RefreshScan{vlist, BLK_AMAX, wp});
+                __syncthreads();
+                if (scanned) {
+                    nv = sc.wcnt[wp];
+                    mv = __int_as_float(sc.wmax[wp]);
+                    wp ^= 1;
+                }
+                stale = false;
+            }
+            uni = false;
+            if (ws && n <= BLK_AMAX) {
+                if (!scanned) {
+                    // no refresh (b = 0, g = S_.j): a scan of its own, the union into ubuf
+                    nu = block_scan_list<T, STD>(j, g, b, a, lam, ubuf, sc, par, nv, mv);
+                }
                 ++cnt.sweeps;
                 if (nv == 0) {
                     inner_ok = true;
                     break;
                 }
+                if (scanned) nu = n + nv;
                 if (nu <= BLK_AMAX && (double)mv >= a.tol) {
+                    if (scanned && tid < 32) warp_union(list, n, vlist, nv, ubuf);
+                    __syncthreads();
                     uni = true;
                     ++rounds;
                     continue;
@@ -1941,7 +2094,9 @@ __device__ void solve_column_block(int j, unsigned char* smem, const CDArgs<T>& 
         }
         if (!inner_ok) status |= COL_NOT_CONVERGED;
         const int n = block_support_list<T>(b, a.p, list, sc, par);
-        double q = block_quadratic_form<T>(j, b, list, n, a, sc);
+        double q;
+        if (!block_quadratic_form_saa<T>(j, b, n, saa_list, sc.saa_n, saa, a, sc, q))
+            q = block_quadratic_form<T>(j, b, list, n, a, sc);
         if (q <= floor2) {
             q = floor2;
             status |= COL_DEGENERATE;
