@@ -63,11 +63,12 @@ WORKLOAD = "batch256"
 N_FITS = 256
 BATCH_PREC = "mixed"
 TOL, MAXIT = 1e-6, 1000
-# kernels of one batched mixed step: coefficient-row and Theta zeroing (side
-# stream), split/transpose, tcgen05 Gram, prep_diag, prep_matrix, column order,
-# block solver over the heavy columns (second side stream), lazy solver,
-# block solver over the handed-over columns, Theta
-KERNELS_PER_STEP = 11
+# kernels of one batched mixed step: split/transpose, tcgen05 Gram, prep_diag,
+# prep_matrix, the column order (heat histogram, offsets, scatter), lazy
+# solver, block solver over the handed-over columns, Theta.  (A batch with a
+# fit of 4096 or more columns adds the block solver over the heavy columns on
+# a side stream; no fit of this workload is that large.)
+KERNELS_PER_STEP = 10
 # fits of the batch the oracle solves (accuracy, CPU baseline, reference arm)
 ORACLE_SAMPLE = list(range(N_FITS))
 REFERENCE_SAMPLE = list(range(0, N_FITS, 32))
@@ -370,28 +371,35 @@ def run_ours(args):
     btd.close()
 
     # ---- end to end through the C ABI with host buffers (pinned): every step
-    # copies its 256 X in and its 256 Theta and sigma out; two batches on two
-    # streams take the steps in turn, so one step's copies run under the next
-    # step's compute
-    Xh = [torch.from_numpy(pr.X).pin_memory() for pr in probs]
-    bt2 = sp.Batch([(X.clone(), lam) for X, lam in inputs], kind="X", precision=BATCH_PREC,
-                   tol=TOL, maxit=MAXIT, use_graph=True, warps_per_block=best_w)
-    slots = [bt, bt2]
+    # copies its 256 X in and its 256 Theta and sigma out.  The 256 X of a
+    # batch sit in one buffer, and its outputs in one buffer each (Batch lays
+    # them out so), so a step is one host-to-device copy, the graph replay and
+    # two device-to-host copies; two batches on two streams take the steps in
+    # turn, so one step's copies run under the next step's compute
+    xshapes = [tuple(pr.X.shape) for pr in probs]
+    Xh_buf, Xh = sp.aligned_views(xshapes, torch.float32, None, pin=True)
+    for d, pr in enumerate(probs):
+        Xh[d].copy_(torch.from_numpy(pr.X))
+    slots, xbufs = [], []
+    for _ in range(2):
+        xb, xv = sp.aligned_views(xshapes, torch.float32, dev)
+        xb.copy_(Xh_buf)
+        xbufs.append(xb)
+        slots.append(sp.Batch([(x, lam) for x, (_, lam) in zip(xv, inputs)], kind="X",
+                              precision=BATCH_PREC, tol=TOL, maxit=MAXIT, use_graph=True,
+                              warps_per_block=best_w))
     streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
-    Th = [[torch.empty((pr.p, pr.p), dtype=torch.float64).pin_memory() for pr in probs]
-          for _ in range(2)]
-    sh = [[torch.empty(pr.p, dtype=torch.float64).pin_memory() for pr in probs] for _ in range(2)]
+    Th = [torch.empty_like(slots[0].Theta_buf, device="cpu").pin_memory() for _ in range(2)]
+    sh = [torch.empty_like(slots[0].sigma_buf, device="cpu").pin_memory() for _ in range(2)]
 
     def e2e_step(i):
         k = i % 2
         b, s = slots[k], streams[k]
         with torch.cuda.stream(s):
-            for d in range(N_FITS):
-                b.inputs[d].copy_(Xh[d], non_blocking=True)
+            xbufs[k].copy_(Xh_buf, non_blocking=True)
             b.run(s)
-            for d in range(N_FITS):
-                Th[k][d].copy_(b.Theta[d], non_blocking=True)
-                sh[k][d].copy_(b.sigma[d], non_blocking=True)
+            Th[k].copy_(b.Theta_buf, non_blocking=True)
+            sh[k].copy_(b.sigma_buf, non_blocking=True)
 
     for i in range(args.warmup):
         e2e_step(i)
@@ -406,11 +414,13 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     if world > 1:
         dist.barrier()
-    h2d = sum(pr.n * pr.p * 4 for pr in probs)
-    d2h = sum(pr.p * pr.p * 8 + pr.p * 8 for pr in probs)
+    h2d = Xh_buf.numel() * 4
+    d2h = (Th[0].numel() + sh[0].numel()) * 8
     e2e = {"value": whole_job_rate(N_FITS * args.steps, world, e2e_s * 1e3), "unit": "solves/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "pipeline": "two batches on two streams in turn; host waits at the end"}
+           "pipeline": "per step one copy of the 256 X in, the graph replay, one copy of the "
+                       "256 Theta and one of the 256 sigma out (fits on 256-byte boundaries); "
+                       "two batches on two streams in turn; host waits at the end"}
     # the link that bounds it: one more copy of a step's Theta bytes into
     # pinned host memory (best of 3)
     lk_src = torch.zeros(d2h // 8, dtype=torch.float64, device=dev)
@@ -427,8 +437,16 @@ def run_ours(args):
     e2e["link_d2h_gbs"] = link_gbs
     e2e["link_ceiling_solves_per_s"] = world * N_FITS * link_gbs * 1e9 / d2h
     e2e["frac_of_link_ceiling"] = e2e["value"] / e2e["link_ceiling_solves_per_s"]
-    del lk_src, lk_dst, Th, sh, Xh
-    bt2.close()
+    # the last step's results as the host got them equal the device-timed batch's
+    last = (args.steps - 1) % 2
+    for d in (0, N_FITS // 2, N_FITS - 1):
+        o = slots[last].Theta[d].data_ptr() - slots[last].Theta_buf.data_ptr()
+        host = Th[last][o // 8:o // 8 + probs[d].p ** 2].view(probs[d].p, probs[d].p)
+        if not torch.equal(host, bt.Theta[d].cpu()):
+            raise RuntimeError("end-to-end results differ from the device-timed batch")
+    del lk_src, lk_dst, Th, sh, Xh, Xh_buf, xbufs
+    for b in slots:
+        b.close()
 
     if rank != 0:
         if world > 1:
@@ -907,9 +925,10 @@ def run_single(args):
                         "p99_ms": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]},
             "roofline": roof, "roofline_gram": roof_gram,
             # Gram (split + tcgen05, or SIMT); prep_diag, prep_matrix, [column
-            # order], [block solver on the heavy columns], lazy, block solver on
-            # the handed-over columns, row count, Theta zeroing, Theta
-            "gpu_launches": ((2 if prec == sp.MIXED else 1) + 7 + (1 if p >= 4096 else 0)
+            # order: more columns than resident warps, or heavy routing],
+            # [block solver on the heavy columns: p >= 4096], lazy, block solver
+            # on the handed-over columns, row count, Theta
+            "gpu_launches": ((2 if prec == sp.MIXED else 1) + 6 + (1 if p >= 4096 else 0)
                              + (1 if p >= 3648 else 0)) * args.steps,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

@@ -567,12 +567,34 @@ def spmesl_batch_destroy(batch) -> None:
     lib().spmesl_batch_destroy(batch)
 
 
+def aligned_views(shapes, dtype, device, pin=False, align=256):
+    """One buffer holding a tensor of each of ``shapes``, every tensor starting
+    on an ``align``-byte boundary; returns (buffer, [views]).  With ``pin`` the
+    buffer is pinned host memory (``device`` is then ignored)."""
+    import math
+    import torch
+    es = torch.empty((), dtype=dtype).element_size()
+    step = max(1, align // es)
+    offs, total = [], 0
+    for sh in shapes:
+        offs.append(total)
+        total += -(-math.prod(sh) // step) * step
+    if pin:
+        buf = torch.empty(max(total, 1), dtype=dtype).pin_memory()
+    else:
+        buf = torch.empty(max(total, 1), dtype=dtype, device=device)
+    return buf, [buf[o:o + math.prod(sh)].view(sh) for o, sh in zip(offs, shapes)]
+
+
 class Batch:
     """Owning wrapper of a batch handle, its workspace and its outputs.
 
     ``inputs`` is a list of (tensor, lambda0) where the tensor is either the
     n x p data X (``kind='X'``) or the p x p covariance S (``kind='S'``);
-    outputs ``Theta[i]`` / ``sigma[i]`` are allocated here."""
+    outputs ``Theta[i]`` / ``sigma[i]`` are allocated here, as views of one
+    buffer each (``Theta_buf`` / ``sigma_buf``, every fit's block starting on
+    a 256-byte boundary), so that all results of a batch move to the host in
+    one copy."""
 
     def __init__(self, inputs, kind="X", precision="fp32", tol=1e-6, maxit=1000,
                  use_graph=False, warps_per_block=0, center=False, record_phase_times=False,
@@ -584,7 +606,9 @@ class Batch:
         self.count = len(inputs)
         self.inputs = [t.contiguous() for t, _ in inputs]
         dev = device or self.inputs[0].device
-        self.Theta, self.sigma = [], []
+        ps = [t.shape[1] if kind == "X" else t.shape[0] for t in self.inputs]
+        self.Theta_buf, self.Theta = aligned_views([(p, p) for p in ps], torch.float64, dev)
+        self.sigma_buf, self.sigma = aligned_views([(p,) for p in ps], torch.float64, dev)
         arr = (Problem * self.count)()
         for i, (t, lam) in enumerate(zip(self.inputs, (l for _, l in inputs))):
             if kind == "X":
@@ -592,10 +616,7 @@ class Batch:
             else:
                 p = t.shape[0]
                 n = 0
-            Th = torch.empty((p, p), dtype=torch.float64, device=dev)
-            sg = torch.empty(p, dtype=torch.float64, device=dev)
-            self.Theta.append(Th)
-            self.sigma.append(sg)
+            Th, sg = self.Theta[i], self.sigma[i]
             arr[i] = Problem(t.data_ptr() if kind == "X" else None,
                              t.data_ptr() if kind == "S" else None, n, p, float(lam),
                              Th.data_ptr(), sg.data_ptr())

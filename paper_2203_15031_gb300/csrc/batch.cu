@@ -532,7 +532,8 @@ cudaError_t enqueue_batch(spmesl_batch* b, unsigned char* ws, cudaStream_t st, i
     // with AUTO the heavy columns lead it and go to the block solver
     const bool lazy_order = b->gradient != SPMESL_GRADIENT_EAGER && b->standardize;
     const bool route = b->gradient == SPMESL_GRADIENT_AUTO;
-    const bool heavy = route && lazy_order;
+    // (the heavy launch only where some fit is large enough to route by heat)
+    const bool heavy = route && lazy_order && b->max_p >= heavy_min_p_of(b->heavy_min_p);
     int* heat = reinterpret_cast<int*>(ws + b->off_heat);
     int* order = reinterpret_cast<int*>(ws + b->off_order);
     const int hheat = heavy_heat_of(b->heavy_heat);

@@ -100,6 +100,23 @@ __device__ __forceinline__ T soft(T x, T lam) {
     return x > lam ? x - lam : (x < -lam ? x + lam : T(0));
 }
 
+// The smallest float f >= x.  For a float m, m < x exactly when m < f, so a
+// stop test of a float iterate against the FP64 tolerance needs no FP64
+// arithmetic per test.
+__device__ __forceinline__ float float_at_least(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// md < tol for an iterate of the working precision T (float: against the
+// float threshold tf of float_at_least(tol); double: directly).
+template <typename T>
+__device__ __forceinline__ bool below_tol(T md, double tol, float tf) {
+    if constexpr (sizeof(T) == 4) return md < tf;
+    else return (double)md < tol;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
@@ -969,6 +986,7 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
     }
     int sw = 0;
     unsigned mv = 0;
+    const float tf = float_at_least(a.tol);
     while (sw < a.maxit) {
         ++sw;
         T md = T(0);
@@ -986,7 +1004,7 @@ __device__ int active_phase(int j, Support<T>& s, const CDArgs<T>& a, T lam, T* 
             mv += d != T(0);
             c = cn;
         }
-        if ((double)md < a.tol) {
+        if (below_tol<T>(md, a.tol, tf)) {
             conv = true;
             break;
         }
@@ -1764,6 +1782,7 @@ __device__ int block_active_phase(int j, T* __restrict__ b, const int* __restric
     conv = false;
     int sw = 0;
     unsigned mv = 0;
+    const float tf = float_at_least(a.tol);
     while (sw < a.maxit) {
         ++sw;
         T md = T(0);
@@ -1792,7 +1811,7 @@ __device__ int block_active_phase(int j, T* __restrict__ b, const int* __restric
             c0 = n0;
             c1 = n1;
         }
-        if ((double)md < a.tol) {
+        if (below_tol<T>(md, a.tol, tf)) {
             conv = true;
             break;
         }
