@@ -25,9 +25,10 @@ JSON line fields beyond the base contract:
   accuracy     max|dTheta|/max|Theta| of the batched mixed results against the
                FP64 oracle on every fit of the step, and the largest
                err_est / kkt_viol / dual_gap the device diagnostics state
-  e2e          the same batch through the C ABI with host buffers: every X
-               copied in from pinned memory and every Theta and sigma copied out
-               inside the timed region, two batches on two streams in turn
+  e2e          the same batch through the C ABI with host buffers: the 256 X
+               copied in from one pinned buffer and the 256 Theta and sigma copied
+               out into one each inside the timed region (Batch keeps a batch's
+               outputs in one buffer), two batches on two streams in turn
   roofline     the coordinate-descent launches of a step (the dominant kernels):
                the row-synchronous byte model of the coordinate descent over
                their CUDA-event time against the measured HBM copy bandwidth;
