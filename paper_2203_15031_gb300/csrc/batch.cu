@@ -98,18 +98,20 @@ __global__ void __launch_bounds__(256) batch_gram_kernel(const BatchFit* __restr
                  static_cast<T*>(f.Sg), f.p, (T)(1.0 / (double)f.n), tm, tn);
 }
 
-// Split/transpose of every fit given as X (SPMESL_MIXED): blocks of 32 x 32
-// over each fit's padded sample dimension and columns; blockDim 32 x 8.
+// Split/transpose of every fit given as X (SPMESL_MIXED): blocks of 64
+// samples x 32 columns over each fit's padded sample dimension (a multiple
+// of 64) and columns; blockDim 32 x 8.
 __global__ void batch_split_kernel(const BatchFit* __restrict__ fits,
                                    const int* __restrict__ split_prefix, int count) {
     const int fi = find_fit(split_prefix, count, blockIdx.x);
     const BatchFit& f = fits[fi];
     const int n_pad = tc_pad_n(f.n);
-    const int bx = n_pad / 32;
+    const int bx = n_pad / 64;
     const int idx = blockIdx.x - f.split_start;
-    split_transpose_tile(static_cast<const float*>(f.X), f.n, f.p, f.p,
-                         static_cast<const float*>(f.mu), static_cast<__nv_bfloat16*>(f.XhT),
-                         static_cast<__nv_bfloat16*>(f.XlT), n_pad, (idx % bx) * 32, (idx / bx) * 32);
+    split_transpose_tile64(static_cast<const float*>(f.X), f.n, f.p, f.p,
+                           static_cast<const float*>(f.mu), static_cast<__nv_bfloat16*>(f.XhT),
+                           static_cast<__nv_bfloat16*>(f.XlT), n_pad, (idx % bx) * 64,
+                           (idx / bx) * 32);
 }
 
 template <typename T>
@@ -831,7 +833,7 @@ spmesl_status spmesl_batch_create(const spmesl_problem* probs, int count, double
         f.split_start = split;
         if (q.X && mixed) {
             gram += tc_tile_grid(f.p, TC_BATCH_BN).count();
-            split += (tc_pad_n(f.n) / 32) * ((f.p + 31) / 32);
+            split += (tc_pad_n(f.n) / 64) * ((f.p + 31) / 32);
         } else if (q.X) {
             const int t = (f.p + GRAM_BM - 1) / GRAM_BM;
             gram += t * (t + 1) / 2;

@@ -11,6 +11,7 @@ namespace spmesl {
 
 constexpr int TC_BM = 128;            // accumulator rows = TMEM lanes
 constexpr int TC_NPAD = 64;           // sample dimension padded to the K block
+static_assert(TC_NPAD % 64 == 0, "split_transpose_tile64 takes 64 samples of the padded dimension");
 
 __host__ __device__ inline int tc_pad_n(int n) { return (n + TC_NPAD - 1) / TC_NPAD * TC_NPAD; }
 
@@ -76,6 +77,42 @@ __device__ __forceinline__ void split_transpose_tile(const float* __restrict__ X
             const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
             XhT[(size_t)c * n_pad + i] = h;
             XlT[(size_t)c * n_pad + i] = l;
+        }
+    }
+}
+
+// The same for a block of 64 samples x 32 columns (block shape 32 x 8; i0 a
+// multiple of 64, so with n_pad a multiple of 64 the block's samples are all
+// below n_pad): lane tx writes samples i0 + 2 tx and i0 + 2 tx + 1 of a
+// column as one 4-byte bf16 pair, so a warp stores 128 contiguous bytes.
+// The tile is kept column-major (tile[column][sample], even stride), so the
+// pair is one 8-byte shared-memory read.  Same values as
+// split_transpose_tile.
+__device__ __forceinline__ void split_transpose_tile64(const float* __restrict__ X, int n, int p,
+                                                       int ldx, const float* __restrict__ mu,
+                                                       __nv_bfloat16* __restrict__ XhT,
+                                                       __nv_bfloat16* __restrict__ XlT, int n_pad,
+                                                       int i0, int c0) {
+    __shared__ __align__(16) float tile[32][66];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int cl = c0 + tx;
+    const float m = (mu && cl < p) ? mu[cl] : 0.f;
+    for (int r = ty; r < 64; r += 8) {
+        const int i = i0 + r;
+        float v = 0.f;
+        if (i < n && cl < p) v = X[(size_t)i * ldx + cl] - m;
+        tile[tx][r] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int c = c0 + r, i = i0 + 2 * tx;
+        if (c < p) {
+            const float2 v = *reinterpret_cast<const float2*>(&tile[r][2 * tx]);
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
+            *reinterpret_cast<__nv_bfloat162*>(XhT + (size_t)c * n_pad + i) = __halves2bfloat162(h0, h1);
+            *reinterpret_cast<__nv_bfloat162*>(XlT + (size_t)c * n_pad + i) = __halves2bfloat162(l0, l1);
         }
     }
 }
