@@ -175,3 +175,28 @@ def test_noalloc_limits_match_the_fit_workspace():
     for prec, limit in ((sp.FP32, 2351), (sp.MIXED, 2351), (sp.FP64, 1664)):
         assert sp.spmesl_fit_workspace_bytes(limit, prec) <= cap
         assert sp.spmesl_fit_workspace_bytes(limit + 1, prec) > cap
+
+
+def test_aligned_views_layout():
+    """Batch keeps every fit's Theta and sigma as views of one buffer each
+    (one copy moves a batch's results): every view starts on a 256-byte
+    boundary, has its own shape, and no two views overlap."""
+    import torch
+    shapes = [(3, 3), (50, 50), (1,), (7,), (129, 129), (2, 2)]
+    for dtype in (torch.float64, torch.float32):
+        buf, views = sp.aligned_views(shapes, dtype, "cpu")
+        es = buf.element_size()
+        spans = []
+        for sh, v in zip(shapes, views):
+            assert tuple(v.shape) == sh and v.is_contiguous() and v.dtype == dtype
+            off = (v.data_ptr() - buf.data_ptr())
+            assert off % 256 == 0
+            spans.append((off, off + v.numel() * es))
+            assert off + v.numel() * es <= buf.numel() * es
+        spans.sort()
+        assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+        # writing through a view lands in the buffer, at the view's place
+        buf.zero_()
+        views[1].fill_(2.0)
+        o = (views[1].data_ptr() - buf.data_ptr()) // es
+        assert float(buf.sum()) == 2.0 * 50 * 50 and float(buf[o:o + 2500].sum()) == 5000.0
