@@ -126,7 +126,8 @@ typedef struct {
 typedef struct {
     int32_t status;             /* spmesl_status of the fit */
     int32_t outer_iters;        /* max over columns of sigma iterations (joint rule: global count) */
-    int64_t inner_sweeps;       /* sum over columns of full sweeps (joint rule: global count) */
+    int64_t inner_sweeps;       /* sum over columns of full sweeps, the block solver's certifying
+                                   passes over every coordinate included (joint rule: global count) */
     int64_t moves;              /* coordinate updates that changed some b_kj (one S-row axpy each) */
     int64_t nnz_B;              /* nonzero off-diagonal b_jk at exit */
     int32_t n_not_converged;    /* columns that hit an iteration cap */
@@ -213,7 +214,10 @@ spmesl_status spmesl_gram(const void* X, int n, int p, int ldx, int precision, i
  *      its current support (up to 32 coefficients) to convergence before
  *      every certifying sweep. That sweep holds the support and updates the
  *      other coordinates; the lasso at one sigma has converged when both moved
- *      nothing by tol. The per-column solvers take a safeguarded secant step
+ *      nothing by tol. Heavy columns (up to 64 support coefficients in the
+ *      phase) let the coordinates such a sweep would move join the next
+ *      phase together instead of entering one at a time; with none the lasso
+ *      at that sigma has converged. The per-column solvers take a safeguarded secant step
  *      on the fixed point sigma = F(sigma) of Eq. (14) after its first step.
  *      The stop tests and the returned (b, sigma) pair are those of
  *      Algorithm 1, so the fit ends at the same fixed point within tol;
